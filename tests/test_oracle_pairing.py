@@ -1,0 +1,77 @@
+"""Brute-force pins of the random permutation and of the expected collision
+rate on tiny cells."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+
+def test_permutation_is_sort_by_key_then_rank(oracle_lib):
+    O = oracle_lib
+    xi = np.array([3, 0, 5, 1, 1, 0, 9, 2], dtype=np.int64)
+    perm = O.permutation(42, 7, 13, xi)
+    live = [q for q in range(len(xi)) if xi[q] > 0]
+    want = sorted(live, key=lambda q: (O.sort_key(42, q, 7, 13), q))
+    assert list(perm) == want
+    assert all(xi[q] > 0 for q in perm)
+
+
+def test_order_ties_broken_by_rank(oracle_lib):
+    O = oracle_lib
+    assert O.order(5, 1, 5, 2) < 0 and O.order(5, 2, 5, 1) > 0
+    assert O.order(4, 9, 5, 1) < 0 and O.order(2**64 - 1, 0, 2**63, 7) > 0
+    assert O.order(7, 3, 7, 3) == 0
+
+
+def test_permutation_uniform_n4(oracle_lib):
+    """All 24 orders of 4 live SDs are equally likely."""
+    O = oracle_lib
+    xi = np.ones(4, dtype=np.int64)
+    counts = {}
+    n = 24000
+    for s in range(n):
+        key = tuple(O.permutation(9, 0, s, xi))
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 24
+    obs = np.array([counts[p] for p in itertools.permutations(range(4))])
+    assert stats.chisquare(obs).pvalue > 1e-4
+
+
+def test_unpaired_uniform_n3(oracle_lib):
+    O = oracle_lib
+    xi = np.array([1, 0, 1, 1], dtype=np.int64)  # rank 1 dead
+    left = np.zeros(4, dtype=np.int64)
+    for s in range(9000):
+        perm = O.permutation(5, 2, s, xi)
+        assert len(perm) == 3 and 1 not in perm
+        left[perm[2]] += 1
+    assert left[1] == 0
+    assert stats.chisquare(left[[0, 2, 3]]).pvalue > 1e-4
+
+
+@pytest.mark.parametrize("n_c", [2, 3, 8, 9])
+def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c):
+    """E[sum of gamma over the drawn pairs] = sum over ALL pairs i<j of
+    K_ij max(xi_i, xi_j) dt/dV: the [n_c(n_c-1)/2]/floor(n_c/2) factor makes
+    floor(n_c/2) random pairs stand for every pair.  Exact expectation by
+    brute force over pairs, versus the mean over 4000 one-step runs."""
+    O = oracle_lib
+    rng = np.random.default_rng(n_c)
+    v = np.exp(rng.uniform(np.log(1e-15), np.log(1e-12), n_c))
+    xi = rng.integers(10**6, 10**7, n_c).astype(np.int64)
+    # every p stays below 1/2: p <= b (2 v_max) xi_max n_c / dV
+    dv = 2.0 * 1500.0 * 2.0 * float(v.max()) * float(xi.max()) * n_c
+    P = O.params("golovin", b=1500.0, dt=1.0, dv=dv)
+    want = sum(1500.0 * (v[i] + v[j]) * max(xi[i], xi[j]) / dv
+               for i in range(n_c) for j in range(i + 1, n_c))
+    tot = 0
+    runs = 4000
+    for seed in range(runs):
+        st = O.State(xi.copy(), v.copy(), np.zeros(n_c, np.int32), None, 1)
+        P.seed = seed
+        tot += O.step(P, st, 0).sum_gamma
+    mean = tot / runs
+    # gamma per pair is Bernoulli(p) with p <= 1/2 here: variance <= want
+    assert abs(mean - want) < 5 * math.sqrt(want / runs)
