@@ -1,0 +1,396 @@
+"""Benchmark of the SDM coalescence step on the 4.19M-super-droplet grid.
+
+Workload: 128 x 128 cells of dV = 1e3 m^3, 256 SDs per cell (4,194,304 SDs),
+lognormal spectrum (geometric-mean radius 15 um, sigma_g 1.4, 1e8 m^-3),
+geometric sweep-out kernel with Rogers-Yau fall speeds, dt = 1 s, FP64.  A
+timed step is one coalescence step of every cell (one kernel launch); the
+dv/dlnr product is taken once at the end of every 600-step run, as in the
+paper's usage (run, then read the product), and its time is included.
+Every 600 steps the run restarts from the initial state (untimed), so the
+timed region always covers the workload's own 600-step evolution.
+
+value   pair-updates/s: sum over timed steps and cells of floor(n_c / 2),
+        divided by the summed CUDA-event time of the steps (state resident,
+        L2 flushed between steps by a 256 MiB write outside the events).
+e2e     the same metric through the C ABI with host buffers: every step
+        sdm_set_attributes from pinned host arrays, one step, and
+        sdm_spectrum into host memory.
+Multi-GPU (torchrun): every rank steps its own replica (weak scaling, no
+collective on the data path).
+
+``--impl reference`` times the oracle (plain C, one core) on a sample of the
+same workload: 1024 of the 16384 cells per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_17238_gb300 import inputs as I  # noqa: E402
+
+METRIC = "SDM pair-updates/s & HBM roofline %; batched vs plain at equal accuracy; p50/p99"
+UNIT = "pair-updates/s"
+RUN_STEPS = 600
+WORKLOAD = ("grid_geometric: 128x128 cells x 256 SDs (4,194,304 SDs), dV=1e3 m^3, lognormal r_g=15um "
+            "sigma_g=1.4 1e8 m^-3, geometric kernel (Rogers-Yau), dt=1 s, 600-step runs, FP64 p, int64 xi")
+KERNEL_NAME = "cell_step_kernel<256,128>"
+PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_17238_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    hsh = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not hsh or hsh.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def pairs_per_step(xi: np.ndarray, cell: np.ndarray, n_cells: int) -> int:
+    live = np.bincount(cell[xi > 0], minlength=n_cells)
+    return int((live // 2).sum())
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank: int, world: int):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2103_17238_gb300 import build as B
+    from paper_2103_17238_gb300 import sdm
+
+    B.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    g = I.grid_geometric(seed=rank)
+    n_sd, n_cells = g.n_sd, g.n_cells
+    cfg = lambda: sdm.make_config("geometric", "fp64", dv=g.dv, n_cells=n_cells, seed=g.seed)
+    pairs0 = pairs_per_step(g.xi, g.cell, n_cells)
+    xi_d = torch.from_numpy(g.xi).to(dev)
+    v_d = torch.from_numpy(g.v).to(dev)
+    cell_d = torch.from_numpy(g.cell).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    spec_d = torch.empty(len(I.R_EDGES) - 1, dtype=torch.float64, device=dev)
+
+    def fresh_run():
+        r = sdm.Run(cfg(), n_sd)
+        r.set_attributes(xi_d, v_d, cell_d)
+        return r
+
+    # warm-up (compiles nothing at run time; warms caches, allocator, clocks)
+    run = fresh_run()
+    for _ in range(args.warmup):
+        run.step(1)
+    run.spectrum(I.R_EDGES, out=spec_d)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    step_ms = []
+    spec_ms = []
+    launches = 0
+    sampler = ClockSampler(dev.index)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    wall0 = time.perf_counter()
+    done = 0
+    while done < K:
+        run.close()
+        run = fresh_run()
+        torch.cuda.synchronize()
+        n = min(RUN_STEPS, K - done)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            ev[i][0].record(stream)
+            run.step(1)
+            ev[i][1].record(stream)
+        flush.zero_()
+        es = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es[0].record(stream)
+        run.spectrum(I.R_EDGES, out=spec_d)
+        es[1].record(stream)
+        torch.cuda.synchronize()
+        step_ms += [a.elapsed_time(b) for a, b in ev]
+        spec_ms.append(es[0].elapsed_time(es[1]))
+        launches += n + 2
+        done += n
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    # pairs: live counts only fall when an SD dies; count them at the end of
+    # the last run (exact when equal to the start)
+    xi_end, v_end = run.attributes()
+    pairs_end = pairs_per_step(xi_end, g.cell, n_cells)
+    pairs_avg = 0.5 * (pairs0 + pairs_end)
+    total_ms = sum(step_ms) + sum(spec_ms)
+    t_local = total_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = pairs_avg * K * world / t_max
+
+    # writes per step (untimed replay of the same steps, counting changed SDs)
+    written = count_written_bytes(run_factory=fresh_run, steps=min(K, RUN_STEPS), torch=torch, sdm=sdm,
+                                  n_sd=n_sd)
+    alg_read = 16 * (n_sd + (n_sd % 2)) + 8 * n_cells
+    alg_bytes = alg_read + written
+    avg_kernel_s = statistics.mean(step_ms) / 1e3
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / avg_kernel_s / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "kernel": KERNEL_NAME, "peak_kind": f"of {peak_kind}",
+                "algorithmic_bytes_per_launch": int(alg_bytes),
+                "frac_of_nominal_8TBps": round(achieved / 8000.0, 4)}
+
+    e2e = measure_e2e(args, g, sdm, torch, pairs0)
+    run.close()
+    res = None
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded lognormal constant-multiplicity sample)",
+            "config": {"workload": WORKLOAD, "n_sd": n_sd, "n_cells": n_cells, "pairs_per_step": pairs0,
+                       "l2": "flushed between timed steps (256 MiB write outside the events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "latency_ms": {"p50": percentile(step_ms, 50), "p99": percentile(step_ms, 99),
+                           "spectrum_ms": statistics.mean(spec_ms)},
+            "roofline": roofline,
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "wall_s_timed_region": wall,
+        }
+    return res
+
+
+def count_written_bytes(run_factory, steps, torch, sdm, n_sd):
+    run = run_factory()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xi_prev = torch.empty(n_sd, dtype=torch.int64, device=dev)
+    v_prev = torch.empty(n_sd, dtype=torch.float64, device=dev)
+    xi_cur = torch.empty_like(xi_prev)
+    v_cur = torch.empty_like(v_prev)
+    sdm.sdm_get_attributes(run.h, xi=xi_prev, volume=v_prev)
+    total = 0
+    for _ in range(steps):
+        run.step(1)
+        sdm.sdm_get_attributes(run.h, xi=xi_cur, volume=v_cur)
+        total += 8 * int((xi_cur != xi_prev).sum().item()) + 8 * int((v_cur != v_prev).sum().item())
+        xi_prev, xi_cur = xi_cur, xi_prev
+        v_prev, v_cur = v_cur, v_prev
+    run.close()
+    return total / steps
+
+
+def measure_e2e(args, g, sdm, torch, pairs0):
+    """set_attributes from pinned host buffers + one step + spectrum to host."""
+    n = max(3, min(args.steps, 50))
+    xi_h = torch.from_numpy(g.xi).pin_memory()
+    v_h = torch.from_numpy(g.v).pin_memory()
+    c_h = torch.from_numpy(g.cell).pin_memory()
+    out = torch.empty(len(I.R_EDGES) - 1, dtype=torch.float64).pin_memory()
+    run = sdm.Run(sdm.make_config("geometric", "fp64", dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+    for _ in range(2):
+        run.set_attributes(xi_h, v_h, c_h).step(1)
+        run.spectrum(I.R_EDGES, out=out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n):
+        run.set_attributes(xi_h, v_h, c_h)
+        run.step(1)
+        run.spectrum(I.R_EDGES, out=out)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / n
+    run.close()
+    h2d = g.n_sd * (8 + 8 + 4)
+    return {"value": pairs0 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 8 * (len(I.R_EDGES) - 1), "ms_per_step": dt * 1e3, "steps": n}
+
+
+def percentile(xs, q):
+    s = sorted(xs)
+    if not s:
+        return None
+    k = (len(s) - 1) * q / 100.0
+    lo, hi = math.floor(k), math.ceil(k)
+    return s[lo] + (s[hi] - s[lo]) * (k - lo)
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """The oracle as it stands (one core) on a bounded sample of the grid."""
+    from oracle import oracle as O
+
+    g = I.grid_geometric(seed=0)
+    n_cells_s = 1024
+    m = g.cell < n_cells_s
+    st = O.State(g.xi[m].copy(), g.v[m].copy(), g.cell[m].copy(), None, n_cells_s)
+    P = O.params("geometric", dv=g.dv, seed=0)
+    pairs = 0
+    t0 = time.perf_counter()
+    s = 0
+    while time.perf_counter() - t0 < seconds and s < RUN_STEPS:
+        pairs += O.step(P, st, s).n_pairs
+        s += 1
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_cells_s} of 16384 cells (262,144 SDs), {s} steps from the initial state, single thread"}
+
+
+# -------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+
+    g = I.grid_geometric(seed=0)
+    n_cells_s = 1024
+    m = g.cell < n_cells_s
+    P = O.params("geometric", dv=g.dv, seed=0)
+    st = O.State(g.xi[m].copy(), g.v[m].copy(), g.cell[m].copy(), None, n_cells_s)
+    for s in range(args.warmup):
+        O.step(P, st, s)
+    st = O.State(g.xi[m].copy(), g.v[m].copy(), g.cell[m].copy(), None, n_cells_s)
+    times, pairs = [], 0
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        pairs += O.step(P, st, s % RUN_STEPS).n_pairs
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = pairs / tot
+    sample = f"{n_cells_s} of 16384 cells (262,144 SDs) per step, single thread"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    # the oracle's timing runs before any CUDA work (no fork after CUDA init)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if res is not None:
+        res["cpu_baseline"] = cpu
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * sdm.h -- C ABI of the GB300 Super-Droplet Method (SDM) coalescence library.
+ *
+ * The library advances the particle-based warm-rain representation of
+ * PySDM v1 (arXiv:2103.17238) by its collision-coalescence dynamic: the SDM
+ * Monte-Carlo algorithm of Shima et al. (2009) named in the paper's
+ * Introduction.  The calls mirror the paper's statement of the problem (API in
+ * brief): a Builder with n_sd super-droplets and a Box(dt, dv) environment,
+ * the Coalescence dynamic with a kernel such as Golovin(b), the attributes
+ * 'volume' and 'n' (multiplicity), Particulator.run(steps), and the
+ * ParticlesVolumeSpectrum product 'dv/dlnr'.
+ *
+ * Conventions shared by every call
+ *   - Every call returns an sdm_status; out-parameters are written only on
+ *     SDM_OK.  sdm_last_error() gives a message for the last failure.
+ *   - Units are SI: volume in m^3, radius in m, dt in s, dv in m^3,
+ *     golovin_b in s^-1.
+ *   - The caller keeps ownership of every array it passes; the library copies
+ *     what it needs before the call returns (or, for device arrays, orders its
+ *     copies on the context's stream before any later work).
+ *   - "on_device" flags say whether a pointer is CUDA device memory (1) or
+ *     host memory (0).  Host buffers may be pageable or pinned.
+ *   - All device work is ordered on the CUDA stream given to sdm_create.
+ *     sdm_coalescence_step only enqueues work and returns; calls that hand
+ *     results to host memory synchronise that stream first.
+ *   - A CUDA error leaves the context unusable: the failing call returns
+ *     SDM_ECUDA and every later call on that context SDM_ESTATE.
+ *   - Contexts are not thread-safe: one thread at a time per context.
+ */
+#ifndef SDM_H
+#define SDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDM_OK = 0,
+    SDM_EINVAL = 1,   /* an argument or attribute value is out of range */
+    SDM_ENOMEM = 2,   /* device or host allocation failed */
+    SDM_ECUDA = 3,    /* a CUDA call failed (context now unusable) */
+    SDM_ESTATE = 4,   /* call not valid in the context's state */
+    SDM_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+    SDM_EBUDGET = 6   /* request exceeds the configured memory budget */
+} sdm_status;
+
+/* Collision kernels K(j, k) in m^3 s^-1 (paper: Usage examples, Box
+ * environment examples -- the Golovin additive kernel, with its analytic
+ * solution, and Berry's geometric sweep-out kernel). */
+typedef enum {
+    SDM_KERNEL_GOLOVIN = 0,  /* K = b (v_j + v_k) */
+    SDM_KERNEL_GEOMETRIC = 1 /* K = pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)|, E = 1,
+                                v_t from Rogers & Yau (1989), r = (3 v / 4 pi)^(1/3) */
+} sdm_kernel;
+
+/* Precision of the kernel K and probability p.  Multiplicities are always
+ * exact int64 and volumes binary64 in both modes. */
+typedef enum {
+    SDM_PREC_FP64 = 0, /* K and p in binary64 */
+    SDM_PREC_KFP32 = 1 /* K and p in binary32, widened to binary64 for gamma */
+} sdm_precision;
+
+/* Device allocator hooks.  alloc returns device memory of at least `bytes`
+ * usable on `stream` (or NULL on failure); free releases it.  Both NULL: the
+ * library uses cudaMallocAsync / cudaFreeAsync on the context's stream. */
+typedef void *(*sdm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*sdm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+typedef struct sdm_config {
+    int32_t kernel;    /* sdm_kernel */
+    int32_t precision; /* sdm_precision */
+    double golovin_b;  /* s^-1 (Golovin only), >= 0 */
+    double dt;         /* timestep, s, > 0 */
+    double dv;         /* volume of one cell, m^3, > 0 */
+    /* Rogers-Yau terminal velocity: k1 r^2 for r < r1, k2 r for r < r2,
+     * k3 sqrt(r) otherwise.  sdm_config_default sets k1 = 1.19e8 m^-1 s^-1,
+     * k2 = 8e3 s^-1, k3 = 201 m^0.5 s^-1, r1 = 40e-6 m, r2 = 600e-6 m. */
+    double ry_k1, ry_k2, ry_k3, ry_r1, ry_r2;
+    int32_t n_cells;   /* cells of this run, >= 1 */
+    int32_t reserved0; /* must be 0 */
+    uint64_t seed;     /* Philox4x32-10 key of this run's random streams */
+    int64_t step0;     /* index of the first step (resume: steps already done) */
+    sdm_alloc_fn alloc;
+    sdm_free_fn free;
+    void *alloc_user;
+} sdm_config;
+
+/* Fills *cfg with the paper's worked example: Golovin b = 1500 s^-1,
+ * dt = 1 s, dv = 1e6 m^3, one cell, FP64, seed 0, step0 0, the Rogers-Yau
+ * defaults, default allocator. */
+void sdm_config_default(sdm_config *cfg);
+
+typedef struct sdm_ctx sdm_ctx;     /* one run: its super-droplets and cells */
+typedef struct sdm_batch sdm_batch; /* several runs stepped by fused launches */
+
+/* Creates a run (the Builder/Particulator of the paper's API in brief) with
+ * room for capacity_sd super-droplets.  cuda_stream is a cudaStream_t (NULL:
+ * the legacy default stream).  The context owns its device memory.
+ * Errors: SDM_EINVAL (bad config or capacity < 1), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_stream, sdm_ctx **out);
+
+/* Sets the super-droplet attributes (the paper's attributes 'n' and
+ * 'volume', plus the cell of each SD).  SD i of the arrays is the SD with
+ * id i; within a cell, SDs keep their order of increasing id (the SD's rank,
+ * which addresses its random sort key).
+ *   xi[n_sd]      int64 multiplicity, >= 0 (0 marks a dead SD)
+ *   volume[n_sd]  binary64 volume in m^3, finite, in [1e-30, 1e30]
+ *   cell_id[n_sd] int32 cell in [0, n_cells)
+ * n_sd in [1, capacity_sd].  Replaces any earlier state; the step counter is
+ * kept.  Errors: SDM_EINVAL (names the first offending SD), SDM_ECUDA. */
+sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, const double *volume,
+                              const int32_t *cell_id, int on_device);
+
+/* Enqueues n_steps >= 0 coalescence steps on the context's stream (the
+ * paper's Particulator.run(steps) with Coalescence as the only dynamic).
+ * Step s, per cell c with n_c live SDs (xi > 0):
+ *   1. key_i = Philox4x32-10(key = seed, ctr = (rank_i >> 1, c, s_lo,
+ *      s_hi | 0 << 31)), words (0,1) for even rank, (2,3) for odd; the live
+ *      SDs are ordered by (key, rank);
+ *   2. neighbours form floor(n_c / 2) pairs l, (j, k) with xi_j >= xi_k
+ *      (ties: j is the earlier of the two);
+ *   3. p = K(j,k) xi_j dt/dv [n_c (n_c - 1) / 2] / floor(n_c / 2);
+ *      u = 53-bit uniform from ctr = (l >> 1, c, s_lo, s_hi | 1 << 31);
+ *      gamma = min(ceil(p - u), floor(xi_j / xi_k));
+ *   4. gamma > 0: xi_j -= gamma xi_k, v_k += gamma v_j; if that leaves
+ *      xi_j = 0 the k SD is split: xi_j = floor(xi_k / 2),
+ *      xi_k -= floor(xi_k / 2), v_j = v_k = v_k + gamma v_j.
+ * Returns without waiting for the GPU.  Errors: SDM_ESTATE (no attributes
+ * set), SDM_EINVAL (n_steps < 0), SDM_ECUDA. */
+sdm_status sdm_coalescence_step(sdm_ctx *ctx, int32_t n_steps);
+
+/* The ParticlesVolumeSpectrum product dv/dlnr of the paper's API in brief:
+ * for radius bins [r_edges[b], r_edges[b+1]) (r = (3 v / 4 pi)^(1/3)), the
+ * volume sum(xi v) of live SDs per m^3 of air per unit ln r.
+ *   per_cell = 0: out[n_edges - 1], all cells, divided by dv * n_cells;
+ *   per_cell = 1: out[n_cells * (n_edges - 1)], cell-major, divided by dv.
+ * r_edges: host array, n_edges >= 2, strictly increasing, > 0.  out: caller
+ * buffer, host (out_on_device = 0; the call synchronises the stream) or
+ * device (ordered on the stream).  Errors: SDM_EINVAL, SDM_ESTATE, SDM_ECUDA. */
+sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, int per_cell, double *out,
+                        int out_on_device);
+
+/* Copies the current multiplicities and volumes of all n_sd SDs, in SD-id
+ * order (dead SDs included, with xi = 0), into caller buffers xi[n_sd] and
+ * volume[n_sd] (either may be NULL).  Host buffers: synchronises the stream.
+ * With sdm_set_attributes and sdm_config.step0 this checkpoints and resumes a
+ * run bit for bit.  Errors: SDM_ESTATE, SDM_ECUDA. */
+sdm_status sdm_get_attributes(sdm_ctx *ctx, int64_t *xi, double *volume, int on_device);
+
+typedef struct sdm_info {
+    int64_t n_sd;          /* SDs set by sdm_set_attributes */
+    int64_t capacity_sd;   /* room reserved at sdm_create */
+    int64_t step;          /* index of the next step */
+    int64_t device_bytes;  /* device memory held by the context */
+    int32_t n_cells;
+    int32_t largest_cell;  /* SDs in the most populated cell */
+} sdm_info;
+
+sdm_status sdm_get_info(const sdm_ctx *ctx, sdm_info *out);
+
+/* Device bytes a context with this capacity and cell count holds (the
+ * serving loop admits runs by this footprint). */
+int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t largest_cell);
+
+/* Releases the context and its device memory (after the stream's pending
+ * work).  NULL is a no-op. */
+sdm_status sdm_destroy(sdm_ctx *ctx);
+
+/* Message for the last failed call on ctx, or of the calling thread when
+ * ctx is NULL.  Never NULL; valid until the next call on the same object. */
+const char *sdm_last_error(const sdm_ctx *ctx);
+
+/* ---- batching: many independent runs (ensemble members, served requests)
+ * advanced by fused launches.  A batch refers to its contexts, which must
+ * stay alive and keep their attributes while the batch exists; every
+ * context keeps its own seed, step counter, kernel, dt and dv, so a batched
+ * step gives bit-for-bit the result of stepping each context alone. */
+
+/* use_graph != 0: sdm_batch_step replays a captured CUDA graph of
+ * graph_steps launches where it can (graph_steps <= 0: 16). */
+sdm_status sdm_batch_create(sdm_ctx *const *ctxs, int32_t n_ctx, void *cuda_stream, int32_t use_graph,
+                            int32_t graph_steps, sdm_batch **out);
+
+/* Enqueues n_steps steps of every context in the batch on the batch's
+ * stream; the contexts' streams are not used.  Errors: SDM_EINVAL,
+ * SDM_ESTATE, SDM_ECUDA. */
+sdm_status sdm_batch_step(sdm_batch *batch, int32_t n_steps);
+
+sdm_status sdm_batch_destroy(sdm_batch *batch);
+
+const char *sdm_batch_last_error(const sdm_batch *batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDM_H */

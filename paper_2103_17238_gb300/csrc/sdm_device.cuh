@@ -1,0 +1,288 @@
+// Device arithmetic of one SDM coalescence step: Philox4x32-10 streams, the
+// cube root, Rogers-Yau terminal velocity, collision kernels, the collision
+// count gamma and the Shima update.
+//
+// GB300 note.  Blackwell Ultra runs binary64 at a small fraction of its
+// binary32 rate, yet the step must reproduce a binary64 definition bit for
+// bit.  Each pair therefore first evaluates p in binary32 together with a
+// rigorous bound on its distance from the binary64 value; when
+// p + bound < u the pair certainly has gamma = 0 (the common case: p is a
+// few percent) and nothing else is computed.  Only pairs that may collide
+// run the exact binary64 evaluation, with explicit round-to-nearest
+// intrinsics so that no multiply-add is contracted.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sdm {
+
+enum : int32_t { KERNEL_GOLOVIN = 0, KERNEL_GEOMETRIC = 1 };
+enum : int32_t { PREC_FP64 = 0, PREC_KFP32 = 1 };
+
+// Per-run parameters, one record per context in device memory.
+struct InstDev {
+    int64_t *xi;             // multiplicities, storage order
+    double *v;               // volumes, storage order
+    const int32_t *cell_off; // n_cells + 1 storage offsets (every cell starts at an even slot)
+    uint64_t seed;
+    int64_t step;            // index of the next step
+    double dtdv;             // dt / dv
+    double b;                // Golovin constant
+    double k1, k2, k3, r1, r2;
+    float bf, k1f, k2f, k3f, r1f, r2f; // binary32 roundings of the above
+    int32_t kernel, precision, n_cells, pad_;
+};
+
+struct WorkItem {
+    int32_t inst; // index into the batch's table of InstDev pointers
+    int32_t cell; // cell within that run
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// products with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
+                       (uint32_t)p0);
+    }
+    return c;
+}
+
+// Stream layout: ctr = (index >> 1, cell, s_lo, s_hi31 | tag << 31),
+// key = seed.  Tag 0: sort keys by SD rank; tag 1: pair uniforms by pair.
+__device__ __forceinline__ uint4 draw4(uint64_t seed, uint32_t half_index, uint32_t cell, int64_t s,
+                                       uint32_t tag)
+{
+    const uint4 c = make_uint4(half_index, cell, (uint32_t)((uint64_t)s),
+                               ((uint32_t)((uint64_t)s >> 32) & 0x7FFFFFFFu) | (tag << 31));
+    return philox4x32_10(c, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// 53-bit uniform m * 2^-53 from the word pair (wa, wb).
+__device__ __forceinline__ double uniform53(uint32_t wa, uint32_t wb)
+{
+    const uint64_t m = ((uint64_t)wa << 21) | (uint64_t)(wb >> 11);
+    return __dmul_rn(__ull2double_rn(m), 0x1p-53);
+}
+
+// A binary32 lower bound of the same uniform: its top 24 bits, exactly.
+__device__ __forceinline__ float uniform_lo24(uint32_t wa) { return __uint2float_rn(wa >> 8) * 0x1p-24f; }
+
+// ------------------------------------------------------------- cube root
+// The library's cube root is a fixed sequence of IEEE operations so that its
+// result is reproducible: x = f 2^E (f in [1,2)), E = 3k + j, m = f 2^j in
+// [1,8); a quadratic seed for f^(-1/3) scaled by 2^(-j/3), two binary32
+// Newton steps for m^(-1/3) (z += z (1 - m z^3) / 3); then y = m z^2 and
+// R = z^2 / 3, two binary64 steps y -= (y^3 - m) R, and y 2^k.
+// Binary64 result within 1 ulp; binary32 twin within 1 ulp.
+constexpr float kCbrtP0 = 0x1.610e12p+0f;
+constexpr float kCbrtP1 = -0x1.e43e5cp-2f;
+constexpr float kCbrtP2 = 0x1.72f4a4p-4f;
+constexpr float kThirdF = 0x1.555556p-2f;
+constexpr double kPi = 0x1.921fb54442d18p+1;      // pi rounded to binary64
+constexpr double kVolToR3 = 0x1.e8ec8a4aeacc4p-3; // 0.75 / pi in binary64
+constexpr float kPiF = 0x1.921fb6p+1f;            // the binary64 pi rounded to binary32
+constexpr float kVolToR3F = 0x1.e8ec8ap-3f;       // 0.75 / pi rounded to binary32
+
+__device__ __forceinline__ float inv_cbrt_seed(float ff, float mf, int j)
+{
+    const float cj = (j == 0) ? 1.0f : ((j == 1) ? 0x1.965feap-1f : 0x1.428a30p-1f);
+    float z = __fmul_rn(kCbrtP2, ff);
+    z = __fadd_rn(kCbrtP1, z);
+    z = __fmul_rn(ff, z);
+    z = __fadd_rn(kCbrtP0, z);
+    z = __fmul_rn(z, cj);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        float t = __fmul_rn(z, z);
+        t = __fmul_rn(t, z);
+        t = __fmul_rn(mf, t);
+        t = __fsub_rn(1.0f, t);
+        t = __fmul_rn(t, z);
+        t = __fmul_rn(t, kThirdF);
+        z = __fadd_rn(z, t);
+    }
+    return z;
+}
+
+// x: positive normal binary64.
+__device__ __forceinline__ double cbrt_exact(double x)
+{
+    const uint64_t bits = (uint64_t)__double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7FF) - 1023;
+    const int k = (E + 3069) / 3 - 1023;
+    const int j = E - 3 * k;
+    const uint64_t mant = bits & 0x000FFFFFFFFFFFFFull;
+    const double f = __longlong_as_double((long long)(mant | (1023ull << 52)));
+    const double m = __longlong_as_double((long long)(mant | ((uint64_t)(1023 + j) << 52)));
+    const float ff = __double2float_rn(f);
+    const float mf = __double2float_rn(m);
+    const float z = inv_cbrt_seed(ff, mf, j);
+    const float zz = __fmul_rn(z, z);
+    double y = (double)__fmul_rn(mf, zz);
+    const double R = (double)__fmul_rn(zz, kThirdF);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        double c = __dmul_rn(y, y);
+        c = __dmul_rn(c, y);
+        c = __dsub_rn(c, m);
+        c = __dmul_rn(c, R);
+        y = __dsub_rn(y, c);
+    }
+    return __dmul_rn(y, __longlong_as_double((long long)((uint64_t)(k + 1023) << 52)));
+}
+
+// x: positive normal binary32.
+__device__ __forceinline__ float cbrt32(float x)
+{
+    const uint32_t bits = __float_as_uint(x);
+    const int E = (int)((bits >> 23) & 0xFF) - 127;
+    const int k = (E + 381) / 3 - 127;
+    const int j = E - 3 * k;
+    const uint32_t mant = bits & 0x007FFFFFu;
+    const float ff = __uint_as_float(mant | (127u << 23));
+    const float mf = __uint_as_float(mant | ((uint32_t)(127 + j) << 23));
+    const float z = inv_cbrt_seed(ff, mf, j);
+    const float zz = __fmul_rn(z, z);
+    float y = __fmul_rn(mf, zz);
+    const float rf = __fmul_rn(zz, kThirdF);
+    float c = __fmul_rn(y, y);
+    c = __fmul_rn(c, y);
+    c = __fsub_rn(c, mf);
+    c = __fmul_rn(c, rf);
+    y = __fsub_rn(y, c);
+    return __fmul_rn(y, __uint_as_float((uint32_t)(k + 127) << 23));
+}
+
+__device__ __forceinline__ double radius_exact(double v) { return cbrt_exact(__dmul_rn(v, kVolToR3)); }
+__device__ __forceinline__ float radius32(float v) { return cbrt32(__fmul_rn(v, kVolToR3F)); }
+
+// ------------------------------------------------------ terminal velocity
+__device__ __forceinline__ double vt_exact(const InstDev &P, double r)
+{
+    if (r < P.r1)
+        return __dmul_rn(P.k1, __dmul_rn(r, r));
+    if (r < P.r2)
+        return __dmul_rn(P.k2, r);
+    return __dmul_rn(P.k3, __dsqrt_rn(r));
+}
+
+__device__ __forceinline__ float vt32(const InstDev &P, float r)
+{
+    if (r < P.r1f)
+        return __fmul_rn(P.k1f, __fmul_rn(r, r));
+    if (r < P.r2f)
+        return __fmul_rn(P.k2f, r);
+    return __fmul_rn(P.k3f, __fsqrt_rn(r));
+}
+
+// --------------------------------------------------------------- p and gamma
+// Exact binary64 probability (the definition).
+__device__ __noinline__ double probability_exact(const InstDev &P, double scale, int64_t xi_j, double vj,
+                                                 double vk)
+{
+    double K;
+    if (P.kernel == KERNEL_GOLOVIN) {
+        K = __dmul_rn(P.b, __dadd_rn(vj, vk));
+    } else {
+        const double rj = radius_exact(vj), rk = radius_exact(vk);
+        const double s = __dadd_rn(rj, rk);
+        K = __dmul_rn(__dmul_rn(kPi, __dmul_rn(s, s)), fabs(__dsub_rn(vt_exact(P, rj), vt_exact(P, rk))));
+    }
+    return __dmul_rn(__dmul_rn(K, __ll2double_rn(xi_j)), scale);
+}
+
+// gamma = min(ceil(p - u), floor(xi_j / xi_k)), the comparison made in
+// binary64 before any integer conversion.
+__device__ __forceinline__ int64_t gamma_exact(double p, double u, int64_t xi_j, int64_t xi_k)
+{
+    const double g = ceil(__dsub_rn(p, u));
+    if (!(g >= 1.0))
+        return 0;
+    const int64_t q = xi_j / xi_k;
+    if (g >= __ll2double_rn(q))
+        return q;
+    return __double2ll_rz(g);
+}
+
+// Collision count of one pair (xi_j >= xi_k > 0).  The binary32 stage is
+// itself the definition in KFP32 mode; in FP64 mode it is a filter: with
+// pf the binary32 value and M a binary32 magnitude of every term of p,
+// |pf - p| <= 2^-18.5 M (error analysis of the operations below, cube root
+// within 1 ulp), so pf + 2^-12 M + 2^-100 < u implies p < u, i.e. gamma = 0.
+// Near a terminal-velocity regime boundary, or when a binary32 value leaves
+// the normal range, the filter abstains and the exact path decides.
+__device__ __forceinline__ int64_t pair_gamma(const InstDev &P, double scale, float scale_f, int64_t xi_j,
+                                              int64_t xi_k, double vj, double vk, uint32_t wa, uint32_t wb)
+{
+    const float u_lo = uniform_lo24(wa);
+    const float vjf = __double2float_rn(vj), vkf = __double2float_rn(vk);
+    const float xjf = __ll2float_rn(xi_j);
+    float pf, mag;
+    bool ok;
+    if (P.kernel == KERNEL_GOLOVIN) {
+        const float K = __fmul_rn(P.bf, __fadd_rn(vjf, vkf));
+        pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
+        mag = pf;
+        ok = K >= 0x1p-126f;
+    } else {
+        const float rj = radius32(vjf), rk = radius32(vkf);
+        const float tj = vt32(P, rj), tk = vt32(P, rk);
+        const float s = __fadd_rn(rj, rk);
+        const float a = __fmul_rn(kPiF, __fmul_rn(s, s));
+        const float K = __fmul_rn(a, fabsf(__fsub_rn(tj, tk)));
+        pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
+        const float km = a * (tj + tk);
+        mag = (km * xjf) * scale_f;
+        const float g1 = P.r1f * 0x1p-16f, g2 = P.r2f * 0x1p-16f;
+        ok = km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f) && fabsf(rj - P.r1f) > g1 &&
+             fabsf(rk - P.r1f) > g1 && fabsf(rj - P.r2f) > g2 && fabsf(rk - P.r2f) > g2;
+    }
+    if (P.precision == PREC_KFP32) {
+        if (pf < u_lo)
+            return 0;
+        return gamma_exact((double)pf, uniform53(wa, wb), xi_j, xi_k);
+    }
+    const float p_hi = pf + mag * 0x1p-12f + 0x1p-100f;
+    if (ok && p_hi < u_lo)
+        return 0;
+    return gamma_exact(probability_exact(P, scale, xi_j, vj, vk), uniform53(wa, wb), xi_j, xi_k);
+}
+
+// Shima update for gamma > 0.  Returns true when the j SD's volume changed
+// (the split case).
+__device__ __forceinline__ bool shima_update(int64_t gamma, int64_t &xi_j, int64_t &xi_k, double &vj, double &vk)
+{
+    const double vnew = __dadd_rn(vk, __dmul_rn(__ll2double_rn(gamma), vj));
+    const int64_t rem = xi_j - gamma * xi_k;
+    if (rem > 0) {
+        xi_j = rem;
+        vk = vnew;
+        return false;
+    }
+    const int64_t h = xi_k / 2;
+    xi_j = h;
+    xi_k = xi_k - h;
+    vj = vnew;
+    vk = vnew;
+    return true;
+}
+
+// dt/dV [n_c (n_c - 1) / 2] / floor(n_c / 2), once per cell.
+__device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
+{
+    const double ratio = __ddiv_rn(__ll2double_rn(n_c * (n_c - 1) / 2), __ll2double_rn(n_c / 2));
+    return __dmul_rn(dtdv, ratio);
+}
+
+} // namespace sdm

@@ -1,0 +1,640 @@
+// Kernels of the SDM coalescence step on sm_103a.
+//
+//  cell_step_kernel<CAP, NT>   one CTA per cell of at most CAP stored SDs:
+//      16-byte vector loads of xi and v into shared memory, in-kernel Philox
+//      sort keys, a one-pass shared-memory bucket sort (keys are uniform, so
+//      bucketing on the top log2(CAP) bits leaves ~1 key per bucket and a
+//      short comparison fix-up finishes the order), pairing, the filtered
+//      collision count, and stores of changed SDs only.
+//  big_*_kernel                cells above the shared-memory capacity: a
+//      histogram pass over chunks, a per-cell scan, a scatter of (key, rank)
+//      into bucket order in global scratch, a per-bucket shared-memory sort
+//      on the next key bits, and a pair pass gathering from the state.
+//  spectrum_kernel             dv/dlnr accumulation per cell or in total.
+//  layout / gather kernels     set_attributes and get_attributes.
+#pragma once
+
+#include "sdm_device.cuh"
+
+namespace sdm {
+
+constexpr int ilog2_c(int x) { return x <= 1 ? 0 : 1 + ilog2_c(x / 2); }
+
+// Exclusive scan, in place, of s[0 .. NITEMS) by NT threads; returns the
+// total to every thread.  Ends with the block synchronised.
+template <int NT, int NITEMS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *s, uint32_t *s_warp)
+{
+    constexpr int E = (NITEMS + NT - 1) / NT;
+    constexpr int NW = NT / 32;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t loc[E];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = t * E + e;
+        loc[e] = idx < NITEMS ? s[idx] : 0u;
+        sum += loc[e];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d)
+            x += y;
+    }
+    if (lane == 31)
+        s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+            if (lane >= d)
+                w += y;
+        }
+        if (lane < NW)
+            s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t base = (warp > 0 ? s_warp[warp - 1] : 0u) + x - sum;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = t * E + e;
+        if (idx < NITEMS)
+            s[idx] = base;
+        base += loc[e];
+    }
+    const uint32_t total = s_warp[NW - 1];
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ra, uint64_t kb, uint32_t rb)
+{
+    return (ka < kb) | ((ka == kb) & (ra < rb));
+}
+
+// -------------------------------------------------------------- cell step
+template <int CAP>
+struct CellSmem {
+    static constexpr size_t bytes = (size_t)CAP * (8 + 8 + 8 + 4 + 2 + 2);
+};
+
+template <int CAP, int NT>
+__global__ void __launch_bounds__(NT) cell_step_kernel(const WorkItem *__restrict__ items,
+                                                       const InstDev *const *__restrict__ insts, int64_t step_offset)
+{
+    constexpr int NB = CAP;
+    constexpr int LB = ilog2_c(CAP);
+    constexpr int RP = (CAP / 2 + NT - 1) / NT; // rank pairs per thread
+    static_assert((1 << LB) == CAP, "CAP must be a power of two");
+    static_assert(CAP <= 65536, "ranks are stored in 16 bits");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int64_t *s_xi = reinterpret_cast<int64_t *>(smem_raw);
+    double *s_v = reinterpret_cast<double *>(s_xi + CAP);
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(s_v + CAP);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_key + CAP);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + NB);
+    uint16_t *s_perm = s_rank + CAP;
+    __shared__ uint32_t s_warp[32];
+    __shared__ double s_scale;
+    __shared__ float s_scale_f;
+
+    const WorkItem it = items[blockIdx.x];
+    const InstDev *__restrict__ P = insts[it.inst];
+    const int32_t off = P->cell_off[it.cell];
+    const int n = P->cell_off[it.cell + 1] - off; // even, <= CAP
+    const int64_t s = P->step + step_offset;
+    const uint64_t seed = P->seed;
+    int64_t *__restrict__ gxi = P->xi + off;
+    double *__restrict__ gv = P->v + off;
+    const int t = threadIdx.x;
+
+    // 1. state into shared memory (16-byte vectors; every cell starts at an even slot)
+    for (int i = t; i < n / 2; i += NT) {
+        const longlong2 a = reinterpret_cast<const longlong2 *>(gxi)[i];
+        const double2 b = reinterpret_cast<const double2 *>(gv)[i];
+        s_xi[2 * i] = a.x;
+        s_xi[2 * i + 1] = a.y;
+        s_v[2 * i] = b.x;
+        s_v[2 * i + 1] = b.y;
+    }
+    for (int i = t; i < NB; i += NT)
+        s_hist[i] = 0u;
+    __syncthreads();
+
+    // 2. sort keys of live SDs and their bucket slots
+    uint64_t key[2 * RP];
+    uint32_t slot[2 * RP];
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+        const int q = t + r * NT;
+        slot[2 * r] = 0xFFFFFFFFu;
+        slot[2 * r + 1] = 0xFFFFFFFFu;
+        key[2 * r] = 0;
+        key[2 * r + 1] = 0;
+        if (2 * q < n) {
+            const bool la = s_xi[2 * q] > 0, lb = s_xi[2 * q + 1] > 0;
+            if (la | lb) {
+                const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)it.cell, s, 0u);
+                if (la) {
+                    key[2 * r] = ((uint64_t)w.x << 32) | w.y;
+                    slot[2 * r] = atomicAdd(&s_hist[key[2 * r] >> (64 - LB)], 1u);
+                }
+                if (lb) {
+                    key[2 * r + 1] = ((uint64_t)w.z << 32) | w.w;
+                    slot[2 * r + 1] = atomicAdd(&s_hist[key[2 * r + 1] >> (64 - LB)], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. bucket starts; the total is the live count n_c
+    const uint32_t n_c = block_exclusive_scan<NT, NB>(s_hist, s_warp);
+    if (n_c < 2)
+        return;
+    if (t == 0) {
+        const double sc = cell_scale(P->dtdv, (int64_t)n_c);
+        s_scale = sc;
+        s_scale_f = __double2float_rn(sc);
+    }
+
+    // 4. scatter into bucket order
+#pragma unroll
+    for (int r = 0; r < RP; ++r) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (slot[2 * r + h] != 0xFFFFFFFFu) {
+                const uint32_t pos = s_hist[key[2 * r + h] >> (64 - LB)] + slot[2 * r + h];
+                s_key[pos] = key[2 * r + h];
+                s_rank[pos] = (uint16_t)(2 * (t + r * NT) + h);
+            }
+        }
+    }
+    __syncthreads();
+
+    // 5. order within each bucket by (key, rank)
+    for (uint32_t pos = t; pos < n_c; pos += NT) {
+        const uint64_t k = s_key[pos];
+        const uint32_t rk = s_rank[pos];
+        const uint32_t b = (uint32_t)(k >> (64 - LB));
+        const uint32_t lo = s_hist[b];
+        const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
+        uint32_t cnt = 0;
+        for (uint32_t m = lo; m < hi; ++m)
+            cnt += key_less(s_key[m], s_rank[m], k, rk) ? 1u : 0u;
+        s_perm[lo + cnt] = (uint16_t)rk;
+    }
+    __syncthreads();
+
+    // 6. pairs (l = 2q, 2q + 1 share one Philox block)
+    const uint32_t n_pairs = n_c / 2;
+    const double scale = s_scale;
+    const float scale_f = s_scale_f;
+    for (uint32_t q = t; 2 * q < n_pairs; q += NT) {
+        const uint4 w = draw4(seed, q, (uint32_t)it.cell, s, 1u);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t l = 2 * q + h;
+            if (l >= n_pairs)
+                break;
+            int a = s_perm[2 * l], b = s_perm[2 * l + 1];
+            int64_t xa = s_xi[a], xb = s_xi[b];
+            if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
+                const int tmp = a;
+                a = b;
+                b = tmp;
+                const int64_t tx = xa;
+                xa = xb;
+                xb = tx;
+            }
+            double va = s_v[a], vb = s_v[b];
+            const int64_t g = pair_gamma(*P, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
+            if (g > 0) {
+                const bool split = shima_update(g, xa, xb, va, vb);
+                gxi[a] = xa;
+                gxi[b] = xb;
+                gv[b] = vb;
+                if (split)
+                    gv[a] = va;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- big cells
+constexpr int kBigChunk = 8192;   // SDs per CTA in the histogram and scatter passes
+constexpr int kBigNT = 1024;
+constexpr int kBigMaxLB = 14;     // at most 16384 top-level buckets
+constexpr int kBucketCap = 2048;  // entries sorted in shared memory per bucket
+constexpr int kBucketNT = 256;
+constexpr int kSubLB = 10;        // second-level buckets inside a bucket
+constexpr int kPairNT = 256;
+
+struct BigCell {
+    int32_t inst, cell;
+    int32_t n;        // stored SDs of the cell
+    int32_t lb;       // log2 of top-level buckets
+    int32_t n_chunks;
+    int32_t pad_;
+    int64_t hist_base; // into the per-(chunk, bucket) count array
+    int64_t sd_base;   // into the key / rank / perm scratch
+    int64_t bkt_base;  // into the bucket-start array (2^lb + 1 entries)
+};
+
+struct BigChunk {
+    int32_t big, chunk;
+};
+struct BigBucket {
+    int32_t big, bucket;
+};
+struct BigPairs {
+    int32_t big, q0; // pair-of-pairs indices q0 .. q0 + kPairNT - 1
+};
+
+struct BigScratch {
+    uint32_t *hist;     // per (chunk, bucket) counts, then prefixes
+    uint32_t *bstart;   // bucket starts per cell, last entry = n_c
+    uint64_t *key;      // keys in bucket order
+    uint32_t *rank;     // ranks in bucket order
+    uint32_t *perm;     // ranks in sorted order
+    double *scale;      // per big cell
+    float *scale_f;
+};
+
+// live SDs of one chunk: keys and their bucket; calls f(key, rank)
+template <typename F>
+__device__ __forceinline__ void big_chunk_keys(const InstDev *P, const BigCell &bc, int chunk, int64_t s,
+                                               const int64_t *gxi, F &&f)
+{
+    const int lo2 = (chunk * kBigChunk) / 2;
+    const int hi2 = min((chunk + 1) * kBigChunk, bc.n) / 2;
+    for (int q = lo2 + (int)threadIdx.x; q < hi2; q += kBigNT) {
+        const longlong2 x = reinterpret_cast<const longlong2 *>(gxi)[q];
+        if ((x.x > 0) | (x.y > 0)) {
+            const uint4 w = draw4(P->seed, (uint32_t)q, (uint32_t)bc.cell, s, 0u);
+            if (x.x > 0)
+                f(((uint64_t)w.x << 32) | w.y, (uint32_t)(2 * q));
+            if (x.y > 0)
+                f(((uint64_t)w.z << 32) | w.w, (uint32_t)(2 * q + 1));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBigNT) big_hist_kernel(const BigChunk *__restrict__ chunks,
+                                                          const BigCell *__restrict__ bigs,
+                                                          const InstDev *const *__restrict__ insts,
+                                                          BigScratch S, int64_t step_offset)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
+    const BigChunk ch = chunks[blockIdx.x];
+    const BigCell bc = bigs[ch.big];
+    const InstDev *P = insts[bc.inst];
+    const int NB = 1 << bc.lb;
+    for (int i = threadIdx.x; i < NB; i += kBigNT)
+        s_hist[i] = 0u;
+    __syncthreads();
+    const int64_t s = P->step + step_offset;
+    const int64_t *gxi = P->xi + P->cell_off[bc.cell];
+    const int sh = 64 - bc.lb;
+    big_chunk_keys(P, bc, ch.chunk, s, gxi, [&](uint64_t k, uint32_t) { atomicAdd(&s_hist[k >> sh], 1u); });
+    __syncthreads();
+    uint32_t *h = S.hist + bc.hist_base + (int64_t)ch.chunk * NB;
+    for (int i = threadIdx.x; i < NB; i += kBigNT)
+        h[i] = s_hist[i];
+}
+
+// One CTA per big cell: per bucket, the running prefix over chunks (in place)
+// and the bucket total; then bucket starts; the cell's scale factor.
+__global__ void __launch_bounds__(kBigNT) big_scan_kernel(const BigCell *__restrict__ bigs,
+                                                          const InstDev *const *__restrict__ insts, BigScratch S)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_tot = reinterpret_cast<uint32_t *>(smem_raw);
+    __shared__ uint32_t s_warp[32];
+    const BigCell bc = bigs[blockIdx.x];
+    const int NB = 1 << bc.lb;
+    uint32_t *h = S.hist + bc.hist_base;
+    for (int b = threadIdx.x; b < NB; b += kBigNT) {
+        uint32_t run = 0;
+        for (int c = 0; c < bc.n_chunks; ++c) {
+            const uint32_t x = h[(int64_t)c * NB + b];
+            h[(int64_t)c * NB + b] = run;
+            run += x;
+        }
+        s_tot[b] = run;
+    }
+    for (int b = NB + threadIdx.x; b < (1 << kBigMaxLB); b += kBigNT)
+        s_tot[b] = 0u;
+    __syncthreads();
+    const uint32_t n_c = block_exclusive_scan<kBigNT, (1 << kBigMaxLB)>(s_tot, s_warp);
+    uint32_t *bs = S.bstart + bc.bkt_base;
+    for (int b = threadIdx.x; b < NB; b += kBigNT)
+        bs[b] = s_tot[b];
+    if (threadIdx.x == 0) {
+        bs[NB] = n_c;
+        const double sc = n_c >= 2 ? cell_scale(insts[bc.inst]->dtdv, (int64_t)n_c) : 0.0;
+        S.scale[blockIdx.x] = sc;
+        S.scale_f[blockIdx.x] = __double2float_rn(sc);
+    }
+}
+
+__global__ void __launch_bounds__(kBigNT) big_scatter_kernel(const BigChunk *__restrict__ chunks,
+                                                             const BigCell *__restrict__ bigs,
+                                                             const InstDev *const *__restrict__ insts,
+                                                             BigScratch S, int64_t step_offset)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem_raw);
+    const BigChunk ch = chunks[blockIdx.x];
+    const BigCell bc = bigs[ch.big];
+    const InstDev *P = insts[bc.inst];
+    const int NB = 1 << bc.lb;
+    for (int i = threadIdx.x; i < NB; i += kBigNT)
+        s_cnt[i] = 0u;
+    __syncthreads();
+    const int64_t s = P->step + step_offset;
+    const int64_t *gxi = P->xi + P->cell_off[bc.cell];
+    const int sh = 64 - bc.lb;
+    const uint32_t *h = S.hist + bc.hist_base + (int64_t)ch.chunk * NB;
+    const uint32_t *bs = S.bstart + bc.bkt_base;
+    uint64_t *kout = S.key + bc.sd_base;
+    uint32_t *rout = S.rank + bc.sd_base;
+    big_chunk_keys(P, bc, ch.chunk, s, gxi, [&](uint64_t k, uint32_t rank) {
+        const uint32_t b = (uint32_t)(k >> sh);
+        const uint32_t pos = bs[b] + h[b] + atomicAdd(&s_cnt[b], 1u);
+        kout[pos] = k;
+        rout[pos] = rank;
+    });
+}
+
+// One CTA per top-level bucket: order its entries by (key, rank) through
+// second-level buckets on the next kSubLB key bits, write the ranks to perm.
+__global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBucket *__restrict__ work,
+                                                                    const BigCell *__restrict__ bigs, BigScratch S)
+{
+    constexpr int NSB = 1 << kSubLB;
+    constexpr int R = kBucketCap / kBucketNT;
+    __shared__ uint32_t s_hist[NSB];
+    __shared__ uint64_t s_key[kBucketCap];
+    __shared__ uint32_t s_rank[kBucketCap];
+    __shared__ uint32_t s_warp[32];
+    const BigBucket bw = work[blockIdx.x];
+    const BigCell bc = bigs[bw.big];
+    const uint32_t *bs = S.bstart + bc.bkt_base;
+    const uint32_t lo = bs[bw.bucket], hi = bs[bw.bucket + 1];
+    const uint32_t nb = hi - lo;
+    const uint64_t *kin = S.key + bc.sd_base + lo;
+    const uint32_t *rin = S.rank + bc.sd_base + lo;
+    uint32_t *pout = S.perm + bc.sd_base + lo;
+    if (nb == 0)
+        return;
+    if (nb > (uint32_t)kBucketCap) {
+        // overfull bucket (never expected for uniform keys): rank by counting
+        for (uint32_t e = threadIdx.x; e < nb; e += kBucketNT) {
+            const uint64_t k = kin[e];
+            const uint32_t r = rin[e];
+            uint32_t cnt = 0;
+            for (uint32_t m = 0; m < nb; ++m)
+                cnt += key_less(kin[m], rin[m], k, r) ? 1u : 0u;
+            pout[cnt] = r;
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < NSB; i += kBucketNT)
+        s_hist[i] = 0u;
+    __syncthreads();
+    const int sh = 64 - bc.lb - kSubLB;
+    uint64_t key[R];
+    uint32_t rank[R], slot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t e = threadIdx.x + r * kBucketNT;
+        slot[r] = 0xFFFFFFFFu;
+        if (e < nb) {
+            key[r] = kin[e];
+            rank[r] = rin[e];
+            slot[r] = atomicAdd(&s_hist[(key[r] >> sh) & (NSB - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    block_exclusive_scan<kBucketNT, NSB>(s_hist, s_warp);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (slot[r] != 0xFFFFFFFFu) {
+            const uint32_t pos = s_hist[(key[r] >> sh) & (NSB - 1)] + slot[r];
+            s_key[pos] = key[r];
+            s_rank[pos] = rank[r];
+        }
+    }
+    __syncthreads();
+    for (uint32_t pos = threadIdx.x; pos < nb; pos += kBucketNT) {
+        const uint64_t k = s_key[pos];
+        const uint32_t rk = s_rank[pos];
+        const uint32_t b = (uint32_t)((k >> sh) & (NSB - 1));
+        const uint32_t blo = s_hist[b];
+        const uint32_t bhi = (b + 1 < (uint32_t)NSB) ? s_hist[b + 1] : nb;
+        uint32_t cnt = 0;
+        for (uint32_t m = blo; m < bhi; ++m)
+            cnt += key_less(s_key[m], s_rank[m], k, rk) ? 1u : 0u;
+        pout[blo + cnt] = rk;
+    }
+}
+
+__global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__restrict__ work,
+                                                            const BigCell *__restrict__ bigs,
+                                                            const InstDev *const *__restrict__ insts,
+                                                            BigScratch S, int64_t step_offset)
+{
+    const BigPairs pw = work[blockIdx.x];
+    const int big = pw.big;
+    const BigCell bc = bigs[big];
+    const uint32_t n_c = S.bstart[bc.bkt_base + (1 << bc.lb)];
+    const uint32_t n_pairs = n_c / 2;
+    const uint32_t q = (uint32_t)pw.q0 + threadIdx.x;
+    if (2 * q >= n_pairs)
+        return;
+    const InstDev *__restrict__ P = insts[bc.inst];
+    const int64_t s = P->step + step_offset;
+    const int32_t off = P->cell_off[bc.cell];
+    int64_t *__restrict__ gxi = P->xi + off;
+    double *__restrict__ gv = P->v + off;
+    const uint32_t *perm = S.perm + bc.sd_base;
+    const double scale = S.scale[big];
+    const float scale_f = S.scale_f[big];
+    const uint4 w = draw4(P->seed, q, (uint32_t)bc.cell, s, 1u);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t l = 2 * q + h;
+        if (l >= n_pairs)
+            break;
+        uint32_t a = perm[2 * l], b = perm[2 * l + 1];
+        int64_t xa = gxi[a], xb = gxi[b];
+        if (xa < xb) {
+            const uint32_t tmp = a;
+            a = b;
+            b = tmp;
+            const int64_t tx = xa;
+            xa = xb;
+            xb = tx;
+        }
+        double va = gv[a], vb = gv[b];
+        const int64_t g = pair_gamma(*P, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
+        if (g > 0) {
+            const bool split = shima_update(g, xa, xb, va, vb);
+            gxi[a] = xa;
+            gxi[b] = xb;
+            gv[b] = vb;
+            if (split)
+                gv[a] = va;
+        }
+    }
+}
+
+// Step counters.  Kernels read base + step_offset, where step_offset is a
+// launch argument; the device base only moves here: by n for every run (the
+// tail of a captured graph), or by a per-run delta (delta != nullptr).
+__global__ void advance_steps_kernel(InstDev *const *insts, int32_t n_inst, int64_t n, const int64_t *delta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_inst)
+        insts[i]->step += delta ? delta[i] : n;
+}
+
+// -------------------------------------------------------------- spectrum
+constexpr int kSpecNT = 256;
+constexpr int kMaxEdges = 1024;
+
+// One CTA per cell: live SDs binned by radius (the exact cube root, so the
+// bin of every SD is the one of the definition), sum(xi v) per bin.
+// per_cell: acc[cell * nb + b]; otherwise atomically into acc[b].
+__global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__restrict__ P, const double *__restrict__ edges,
+                                                           int32_t n_edges, int32_t per_cell, double *__restrict__ acc)
+{
+    __shared__ double s_edges[kMaxEdges];
+    __shared__ double s_acc[kMaxEdges];
+    const int cell = blockIdx.x;
+    const int nb = n_edges - 1;
+    for (int i = threadIdx.x; i < n_edges; i += kSpecNT)
+        s_edges[i] = edges[i];
+    for (int i = threadIdx.x; i < nb; i += kSpecNT)
+        s_acc[i] = 0.0;
+    __syncthreads();
+    const int32_t off = P->cell_off[cell];
+    const int n = P->cell_off[cell + 1] - off;
+    const int64_t *gxi = P->xi + off;
+    const double *gv = P->v + off;
+    const double e0 = s_edges[0], eN = s_edges[n_edges - 1];
+    for (int i = threadIdx.x; i < n; i += kSpecNT) {
+        const int64_t x = gxi[i];
+        if (x <= 0)
+            continue;
+        const double v = gv[i];
+        const double r = radius_exact(v);
+        if (r < e0 || !(r < eN))
+            continue;
+        int lo = 0, hi = n_edges - 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_edges[mid] <= r)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        atomicAdd(&s_acc[lo], __dmul_rn(__ll2double_rn(x), v));
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += kSpecNT) {
+        if (per_cell)
+            acc[(int64_t)cell * nb + b] = s_acc[b];
+        else if (s_acc[b] != 0.0)
+            atomicAdd(&acc[b], s_acc[b]);
+    }
+}
+
+// out[i] = acc[i] / vol / (ln e[b+1] - ln e[b])
+__global__ void spectrum_finalize_kernel(const double *__restrict__ acc, const double *__restrict__ edges,
+                                         int32_t n_edges, int64_t n_out, double vol, double *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out)
+        return;
+    const int nb = n_edges - 1;
+    const int b = (int)(i % nb);
+    out[i] = acc[i] / vol / (log(edges[b + 1]) - log(edges[b]));
+}
+
+// --------------------------------------------------------------- layout
+// Validation and per-cell counts of set_attributes.  flags bit 0: an
+// invalid attribute (first bad SD index in *bad); bit 1: cells not sorted.
+__global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
+                                      const int32_t *__restrict__ cell, int32_t n_cells, uint32_t *__restrict__ counts,
+                                      uint32_t *__restrict__ flags, unsigned long long *__restrict__ bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sd; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = cell[i];
+        const double vi = v[i];
+        const bool ok = xi[i] >= 0 && vi >= 1e-30 && vi <= 1e30 && c >= 0 && c < n_cells;
+        if (!ok) {
+            atomicOr(flags, 1u);
+            atomicMin(bad, (unsigned long long)i);
+            continue;
+        }
+        atomicAdd(&counts[c], 1u);
+        if (i > 0 && cell[i - 1] > c)
+            atomicOr(flags, 2u);
+    }
+}
+
+// Cell-sorted input: SD i goes to padded slot poff[c] + (i - uoff[c]).
+// Otherwise pos[i] gives the slot.
+__global__ void scatter_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
+                               const int32_t *__restrict__ cell, const int32_t *__restrict__ poff,
+                               const int32_t *__restrict__ uoff, const int32_t *__restrict__ pos,
+                               int64_t *__restrict__ sxi, double *__restrict__ sv, int32_t *__restrict__ id_of_slot)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sd; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t p;
+        if (pos) {
+            p = pos[i];
+        } else {
+            const int32_t c = cell[i];
+            p = poff[c] + (int32_t)(i - uoff[c]);
+        }
+        sxi[p] = xi[i];
+        sv[p] = v[i];
+        id_of_slot[p] = (int32_t)i;
+    }
+}
+
+// Padding slots: dead, with a harmless positive volume.
+__global__ void fill_padding_kernel(int64_t n_slots, int64_t *__restrict__ sxi, double *__restrict__ sv,
+                                    int32_t *__restrict__ id_of_slot)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += (int64_t)gridDim.x * blockDim.x) {
+        sxi[i] = 0;
+        sv[i] = 1.0;
+        id_of_slot[i] = -1;
+    }
+}
+
+__global__ void gather_kernel(int64_t n_slots, const int64_t *__restrict__ sxi, const double *__restrict__ sv,
+                              const int32_t *__restrict__ id_of_slot, int64_t *__restrict__ xi, double *__restrict__ v)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_slots; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t id = id_of_slot[p];
+        if (id < 0)
+            continue;
+        if (xi)
+            xi[id] = sxi[p];
+        if (v)
+            v[id] = sv[p];
+    }
+}
+
+} // namespace sdm

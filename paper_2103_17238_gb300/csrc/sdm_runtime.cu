@@ -1,0 +1,938 @@
+// C-ABI runtime of the SDM coalescence library: contexts, attribute layout,
+// batch plans (work lists per cell-size class, big-cell scratch), launches,
+// CUDA-graph replay, the spectrum product.  Declarations and the contract of
+// every call are in include/sdm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sdm.h"
+#include "sdm_kernels.cuh"
+
+using namespace sdm;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+struct DevMem {
+    sdm_alloc_fn fn = nullptr;
+    sdm_free_fn ffn = nullptr;
+    void *user = nullptr;
+    cudaStream_t stream = nullptr;
+
+    void *get(size_t bytes)
+    {
+        if (bytes == 0)
+            bytes = 16;
+        if (fn)
+            return fn(bytes, (void *)stream, user);
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return p;
+    }
+    void put(void *p, size_t bytes)
+    {
+        if (!p)
+            return;
+        if (ffn)
+            ffn(p, bytes, (void *)stream, user);
+        else
+            cudaFreeAsync(p, stream);
+    }
+};
+
+// A device buffer owned through DevMem.
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Cell-size classes of the shared-memory path.
+constexpr int kClassCap[] = {64, 128, 256, 512, 1024, 2048, 4096};
+constexpr int kNumClass = sizeof(kClassCap) / sizeof(kClassCap[0]);
+constexpr int kSmemMaxCell = 4096;
+
+struct Plan {
+    int n_inst = 0;
+    InstDev **d_insts = nullptr; // table of the runs' device records
+    WorkItem *d_items[kNumClass] = {};
+    int n_items[kNumClass] = {};
+    BigCell *d_bigs = nullptr;
+    int n_big = 0;
+    BigChunk *d_chunks = nullptr;
+    int n_chunks = 0;
+    BigBucket *d_buckets = nullptr;
+    int n_buckets = 0;
+    BigPairs *d_pairs = nullptr;
+    int n_pair_blocks = 0;
+    BigScratch scratch{};
+    int max_big_lb = 0;
+    std::vector<Buf> bufs;
+    int64_t bytes = 0;
+};
+
+} // namespace
+
+struct sdm_ctx {
+    sdm_config cfg{};
+    DevMem mem;
+    cudaStream_t stream = nullptr;
+    int64_t capacity_sd = 0;
+    int64_t n_slots_cap = 0;
+    int64_t n_sd = 0;
+    int64_t n_slots = 0;
+    int64_t step = 0;     // index of the next step
+    int64_t dev_base = 0; // value of the device record's step counter
+    int32_t largest_cell = 0;
+    bool has_attributes = false;
+    bool broken = false;
+    std::string error;
+    // device state
+    int64_t *d_xi = nullptr;
+    double *d_v = nullptr;
+    int32_t *d_id_of_slot = nullptr;
+    int32_t *d_cell_off = nullptr;
+    InstDev *d_inst = nullptr;
+    std::vector<int32_t> h_cell_off;
+    int64_t device_bytes = 0;
+    sdm_batch *self_batch = nullptr;
+};
+
+struct sdm_batch {
+    std::vector<sdm_ctx *> ctxs;
+    cudaStream_t stream = nullptr;
+    DevMem mem;
+    Plan plan;
+    bool use_graph = false;
+    int graph_steps = 16;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    int64_t *d_delta = nullptr;       // per-run step deltas for counter syncs
+    std::vector<int64_t> h_delta;
+    std::string error;
+    bool broken = false;
+};
+
+namespace {
+
+sdm_status fail(std::string *slot, sdm_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (slot)
+        *slot = buf;
+    g_thread_error = buf;
+    return st;
+}
+
+sdm_status cuda_fail(sdm_ctx *ctx, cudaError_t e, const char *what)
+{
+    ctx->broken = true;
+    return fail(&ctx->error, SDM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+sdm_status cuda_fail(sdm_batch *b, cudaError_t e, const char *what)
+{
+    b->broken = true;
+    for (sdm_ctx *c : b->ctxs)
+        c->broken = true;
+    return fail(&b->error, SDM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CTX_CUDA(ctx, call)                                                                                            \
+    do {                                                                                                               \
+        cudaError_t e_ = (call);                                                                                       \
+        if (e_ != cudaSuccess)                                                                                         \
+            return cuda_fail((ctx), e_, #call);                                                                        \
+    } while (0)
+
+template <typename T>
+T *plan_alloc(Plan &pl, DevMem &mem, size_t count)
+{
+    Buf b;
+    b.bytes = std::max<size_t>(count * sizeof(T), 16);
+    b.p = mem.get(b.bytes);
+    if (!b.p)
+        return nullptr;
+    pl.bufs.push_back(b);
+    pl.bytes += (int64_t)b.bytes;
+    return static_cast<T *>(b.p);
+}
+
+void plan_free(Plan &pl, DevMem &mem)
+{
+    for (Buf &b : pl.bufs)
+        mem.put(b.p, b.bytes);
+    pl = Plan{};
+}
+
+int big_lb(int n)
+{
+    int lg = 0;
+    while ((1 << lg) < n)
+        ++lg;
+    return std::min(std::max(lg - 8, 1), kBigMaxLB);
+}
+
+size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
+
+template <int CAP, int NT>
+cudaError_t configure_cell_kernel()
+{
+    return cudaFuncSetAttribute(cell_step_kernel<CAP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)CellSmem<CAP>::bytes);
+}
+
+cudaError_t configure_kernels_once()
+{
+    static cudaError_t status = [] {
+        cudaError_t e = cudaSuccess;
+        cudaError_t r;
+        if ((r = configure_cell_kernel<64, 32>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<128, 64>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<256, 128>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<512, 256>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<1024, 512>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<2048, 1024>()) != cudaSuccess) e = r;
+        if ((r = configure_cell_kernel<4096, 1024>()) != cudaSuccess) e = r;
+        const int hb = (int)big_hist_smem(kBigMaxLB);
+        if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
+        if ((r = cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
+        if ((r = cudaFuncSetAttribute(big_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
+        return e;
+    }();
+    return status;
+}
+
+void launch_cell_class(int cls, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
+{
+    switch (cls) {
+    case 0: cell_step_kernel<64, 32><<<n, 32, CellSmem<64>::bytes, st>>>(items, insts, off); break;
+    case 1: cell_step_kernel<128, 64><<<n, 64, CellSmem<128>::bytes, st>>>(items, insts, off); break;
+    case 2: cell_step_kernel<256, 128><<<n, 128, CellSmem<256>::bytes, st>>>(items, insts, off); break;
+    case 3: cell_step_kernel<512, 256><<<n, 256, CellSmem<512>::bytes, st>>>(items, insts, off); break;
+    case 4: cell_step_kernel<1024, 512><<<n, 512, CellSmem<1024>::bytes, st>>>(items, insts, off); break;
+    case 5: cell_step_kernel<2048, 1024><<<n, 1024, CellSmem<2048>::bytes, st>>>(items, insts, off); break;
+    case 6: cell_step_kernel<4096, 1024><<<n, 1024, CellSmem<4096>::bytes, st>>>(items, insts, off); break;
+    }
+}
+
+int class_of(int n)
+{
+    for (int c = 0; c < kNumClass; ++c)
+        if (n <= kClassCap[c])
+            return c;
+    return -1;
+}
+
+// Work lists of every run in the batch, split by cell size.
+sdm_status build_plan(sdm_batch *b)
+{
+    Plan &pl = b->plan;
+    DevMem &mem = b->mem;
+    const int n_inst = (int)b->ctxs.size();
+    std::vector<WorkItem> items[kNumClass];
+    std::vector<BigCell> bigs;
+    std::vector<BigChunk> chunks;
+    std::vector<BigBucket> buckets;
+    std::vector<BigPairs> pairs;
+    std::vector<InstDev *> insts(n_inst);
+    int64_t hist_total = 0, sd_total = 0, bkt_total = 0;
+    for (int i = 0; i < n_inst; ++i) {
+        sdm_ctx *c = b->ctxs[i];
+        insts[i] = c->d_inst;
+        for (int cell = 0; cell < c->cfg.n_cells; ++cell) {
+            const int n = c->h_cell_off[cell + 1] - c->h_cell_off[cell];
+            if (n < 2)
+                continue;
+            const int cls = class_of(n);
+            if (cls >= 0) {
+                items[cls].push_back(WorkItem{i, cell});
+                continue;
+            }
+            BigCell bc{};
+            bc.inst = i;
+            bc.cell = cell;
+            bc.n = n;
+            bc.lb = big_lb(n);
+            bc.n_chunks = (n + kBigChunk - 1) / kBigChunk;
+            bc.hist_base = hist_total;
+            bc.sd_base = sd_total;
+            bc.bkt_base = bkt_total;
+            hist_total += (int64_t)bc.n_chunks << bc.lb;
+            sd_total += n;
+            bkt_total += (1 << bc.lb) + 1;
+            const int big = (int)bigs.size();
+            for (int k = 0; k < bc.n_chunks; ++k)
+                chunks.push_back(BigChunk{big, k});
+            for (int k = 0; k < (1 << bc.lb); ++k)
+                buckets.push_back(BigBucket{big, k});
+            const int n_q = (n / 2 + 1) / 2; // pair-of-pairs upper bound
+            for (int q0 = 0; q0 < n_q; q0 += kPairNT)
+                pairs.push_back(BigPairs{big, q0});
+            pl.max_big_lb = std::max(pl.max_big_lb, bc.lb);
+            bigs.push_back(bc);
+        }
+    }
+    pl.n_inst = n_inst;
+    pl.d_insts = plan_alloc<InstDev *>(pl, mem, n_inst);
+    if (!pl.d_insts)
+        return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
+    cudaError_t e = cudaMemcpyAsync(pl.d_insts, insts.data(), sizeof(InstDev *) * n_inst, cudaMemcpyHostToDevice, b->stream);
+    for (int k = 0; k < kNumClass && e == cudaSuccess; ++k) {
+        pl.n_items[k] = (int)items[k].size();
+        if (!pl.n_items[k])
+            continue;
+        pl.d_items[k] = plan_alloc<WorkItem>(pl, mem, items[k].size());
+        if (!pl.d_items[k])
+            return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
+        e = cudaMemcpyAsync(pl.d_items[k], items[k].data(), sizeof(WorkItem) * items[k].size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    }
+    if (e == cudaSuccess && !bigs.empty()) {
+        pl.n_big = (int)bigs.size();
+        pl.n_chunks = (int)chunks.size();
+        pl.n_buckets = (int)buckets.size();
+        pl.n_pair_blocks = (int)pairs.size();
+        pl.d_bigs = plan_alloc<BigCell>(pl, mem, bigs.size());
+        pl.d_chunks = plan_alloc<BigChunk>(pl, mem, chunks.size());
+        pl.d_buckets = plan_alloc<BigBucket>(pl, mem, buckets.size());
+        pl.d_pairs = plan_alloc<BigPairs>(pl, mem, pairs.size());
+        pl.scratch.hist = plan_alloc<uint32_t>(pl, mem, hist_total);
+        pl.scratch.bstart = plan_alloc<uint32_t>(pl, mem, bkt_total);
+        pl.scratch.key = plan_alloc<uint64_t>(pl, mem, sd_total);
+        pl.scratch.rank = plan_alloc<uint32_t>(pl, mem, sd_total);
+        pl.scratch.perm = plan_alloc<uint32_t>(pl, mem, sd_total);
+        pl.scratch.scale = plan_alloc<double>(pl, mem, bigs.size());
+        pl.scratch.scale_f = plan_alloc<float>(pl, mem, bigs.size());
+        if (!pl.d_bigs || !pl.d_chunks || !pl.d_buckets || !pl.d_pairs || !pl.scratch.hist || !pl.scratch.bstart ||
+            !pl.scratch.key || !pl.scratch.rank || !pl.scratch.perm || !pl.scratch.scale || !pl.scratch.scale_f)
+            return fail(&b->error, SDM_ENOMEM, "batch plan: big-cell scratch allocation failed");
+        e = cudaMemcpyAsync(pl.d_bigs, bigs.data(), sizeof(BigCell) * bigs.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pl.d_chunks, chunks.data(), sizeof(BigChunk) * chunks.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pl.d_buckets, buckets.data(), sizeof(BigBucket) * buckets.size(),
+                                cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(pl.d_pairs, pairs.data(), sizeof(BigPairs) * pairs.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream); // host vectors above go out of scope
+    if (e != cudaSuccess)
+        return cuda_fail(b, e, "batch plan upload");
+    return SDM_OK;
+}
+
+// Enqueues one step (offset `off` from each run's device counter) of every cell.
+void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
+{
+    for (int k = 0; k < kNumClass; ++k)
+        if (pl.n_items[k])
+            launch_cell_class(k, pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
+    if (pl.n_big) {
+        const size_t hs = big_hist_smem(pl.max_big_lb);
+        big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
+        big_scan_kernel<<<pl.n_big, kBigNT, big_hist_smem(kBigMaxLB), st>>>(pl.d_bigs, pl.d_insts, pl.scratch);
+        big_scatter_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
+        big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.scratch);
+        big_pairs_kernel<<<pl.n_pair_blocks, kPairNT, 0, st>>>(pl.d_pairs, pl.d_bigs, pl.d_insts, pl.scratch, off);
+    }
+}
+
+// A captured graph: n steps from the device counters, then the counters advance by n.
+void enqueue_graph_body(const Plan &pl, int32_t n, cudaStream_t st)
+{
+    for (int32_t i = 0; i < n; ++i)
+        enqueue_step(pl, i, st);
+    advance_steps_kernel<<<(pl.n_inst + 255) / 256, 256, 0, st>>>(pl.d_insts, pl.n_inst, n, nullptr);
+}
+
+// Brings every run's device counter up to its host step.
+sdm_status sync_counters(sdm_batch *b)
+{
+    bool any = false;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        b->h_delta[i] = b->ctxs[i]->step - b->ctxs[i]->dev_base;
+        any |= b->h_delta[i] != 0;
+    }
+    if (!any)
+        return SDM_OK;
+    cudaError_t e = cudaMemcpyAsync(b->d_delta, b->h_delta.data(), sizeof(int64_t) * b->ctxs.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(b, e, "step counter sync");
+    advance_steps_kernel<<<(b->plan.n_inst + 255) / 256, 256, 0, b->stream>>>(b->plan.d_insts, b->plan.n_inst, 0,
+                                                                              b->d_delta);
+    for (sdm_ctx *c : b->ctxs)
+        c->dev_base = c->step;
+    return SDM_OK;
+}
+
+sdm_status batch_init(sdm_batch *b, sdm_ctx *const *ctxs, int32_t n_ctx, cudaStream_t stream, int use_graph,
+                      int graph_steps)
+{
+    for (int i = 0; i < n_ctx; ++i) {
+        if (!ctxs[i])
+            return fail(&b->error, SDM_EINVAL, "context %d is NULL", i);
+        if (ctxs[i]->broken)
+            return fail(&b->error, SDM_ESTATE, "context %d is unusable after a CUDA error", i);
+        if (!ctxs[i]->has_attributes)
+            return fail(&b->error, SDM_ESTATE, "context %d has no attributes", i);
+        b->ctxs.push_back(ctxs[i]);
+    }
+    b->stream = stream;
+    b->mem = ctxs[0]->mem;
+    b->mem.stream = stream;
+    b->use_graph = use_graph != 0;
+    b->graph_steps = graph_steps > 0 ? graph_steps : 16;
+    cudaError_t e = configure_kernels_once();
+    if (e != cudaSuccess)
+        return cuda_fail(b, e, "kernel configuration");
+    sdm_status st = build_plan(b);
+    if (st != SDM_OK)
+        return st;
+    b->h_delta.assign(b->ctxs.size(), 0);
+    b->d_delta = plan_alloc<int64_t>(b->plan, b->mem, b->ctxs.size());
+    if (!b->d_delta)
+        return fail(&b->error, SDM_ENOMEM, "batch: device allocation failed");
+    return SDM_OK;
+}
+
+void batch_release(sdm_batch *b)
+{
+    if (b->graph_exec)
+        cudaGraphExecDestroy(b->graph_exec);
+    if (b->capture_stream)
+        cudaStreamDestroy(b->capture_stream);
+    b->graph_exec = nullptr;
+    b->capture_stream = nullptr;
+    plan_free(b->plan, b->mem);
+}
+
+sdm_status batch_step(sdm_batch *b, int32_t n_steps)
+{
+    if (b->broken)
+        return fail(&b->error, SDM_ESTATE, "batch unusable after a CUDA error");
+    if (n_steps < 0)
+        return fail(&b->error, SDM_EINVAL, "n_steps < 0");
+    for (sdm_ctx *c : b->ctxs)
+        if (c->broken)
+            return fail(&b->error, SDM_ESTATE, "a context of the batch is unusable");
+    if (n_steps == 0)
+        return SDM_OK;
+    int32_t left = n_steps;
+    // direct launches need one common offset (host step - device counter)
+    const int64_t pend = b->ctxs[0]->step - b->ctxs[0]->dev_base;
+    bool uniform = true;
+    for (sdm_ctx *c : b->ctxs)
+        uniform &= (c->step - c->dev_base) == pend;
+    const bool graph = b->use_graph && n_steps >= b->graph_steps;
+    if (graph || !uniform) {
+        sdm_status st = sync_counters(b);
+        if (st != SDM_OK)
+            return st;
+    }
+    if (graph) {
+        if (!b->graph_exec) {
+            cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "graph capture stream");
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "cudaStreamBeginCapture");
+            enqueue_graph_body(b->plan, b->graph_steps, b->capture_stream);
+            e = cudaStreamEndCapture(b->capture_stream, &g);
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "cudaGraphInstantiate");
+        }
+        while (left >= b->graph_steps) {
+            cudaError_t e = cudaGraphLaunch(b->graph_exec, b->stream);
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "cudaGraphLaunch");
+            left -= b->graph_steps;
+            for (sdm_ctx *c : b->ctxs) {
+                c->step += b->graph_steps;
+                c->dev_base += b->graph_steps;
+            }
+        }
+    }
+    const int64_t off0 = b->ctxs[0]->step - b->ctxs[0]->dev_base;
+    for (int32_t i = 0; i < left; ++i)
+        enqueue_step(b->plan, off0 + i, b->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(b, e, "step launch");
+    for (sdm_ctx *c : b->ctxs)
+        c->step += left;
+    return SDM_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+sdm_status check_config(const sdm_config *cfg, std::string *err)
+{
+    if (!cfg)
+        return fail(err, SDM_EINVAL, "config is NULL");
+    if (cfg->kernel != SDM_KERNEL_GOLOVIN && cfg->kernel != SDM_KERNEL_GEOMETRIC)
+        return fail(err, SDM_EINVAL, "unknown kernel %d", cfg->kernel);
+    if (cfg->precision != SDM_PREC_FP64 && cfg->precision != SDM_PREC_KFP32)
+        return fail(err, SDM_EINVAL, "unknown precision %d", cfg->precision);
+    if (!(std::isfinite(cfg->golovin_b) && cfg->golovin_b >= 0.0 && cfg->golovin_b <= 1e30))
+        return fail(err, SDM_EINVAL, "golovin_b must be finite and in [0, 1e30]");
+    if (!finite_pos(cfg->dt) || !finite_pos(cfg->dv))
+        return fail(err, SDM_EINVAL, "dt and dv must be finite and > 0");
+    if (!finite_pos(cfg->ry_k1) || !finite_pos(cfg->ry_k2) || !finite_pos(cfg->ry_k3) || !finite_pos(cfg->ry_r1) ||
+        !(cfg->ry_r2 > cfg->ry_r1) || !std::isfinite(cfg->ry_r2))
+        return fail(err, SDM_EINVAL, "Rogers-Yau coefficients must be finite, > 0, r1 < r2");
+    if (cfg->n_cells < 1)
+        return fail(err, SDM_EINVAL, "n_cells must be >= 1");
+    if (cfg->reserved0 != 0)
+        return fail(err, SDM_EINVAL, "reserved0 must be 0");
+    if (cfg->step0 < 0)
+        return fail(err, SDM_EINVAL, "step0 must be >= 0");
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return fail(err, SDM_EINVAL, "alloc and free must be given together");
+    return SDM_OK;
+}
+
+InstDev make_inst(const sdm_ctx *c)
+{
+    InstDev d{};
+    d.xi = c->d_xi;
+    d.v = c->d_v;
+    d.cell_off = c->d_cell_off;
+    d.seed = c->cfg.seed;
+    d.step = c->step;
+    d.dtdv = c->cfg.dt / c->cfg.dv;
+    d.b = c->cfg.golovin_b;
+    d.k1 = c->cfg.ry_k1;
+    d.k2 = c->cfg.ry_k2;
+    d.k3 = c->cfg.ry_k3;
+    d.r1 = c->cfg.ry_r1;
+    d.r2 = c->cfg.ry_r2;
+    d.bf = (float)d.b;
+    d.k1f = (float)d.k1;
+    d.k2f = (float)d.k2;
+    d.k3f = (float)d.k3;
+    d.r1f = (float)d.r1;
+    d.r2f = (float)d.r2;
+    d.kernel = c->cfg.kernel;
+    d.precision = c->cfg.precision;
+    d.n_cells = c->cfg.n_cells;
+    return d;
+}
+
+sdm_status ctx_usable(sdm_ctx *ctx)
+{
+    if (!ctx)
+        return fail(nullptr, SDM_EINVAL, "context is NULL");
+    if (ctx->broken)
+        return fail(&ctx->error, SDM_ESTATE, "context unusable after a CUDA error");
+    return SDM_OK;
+}
+
+} // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void sdm_config_default(sdm_config *cfg)
+{
+    if (!cfg)
+        return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->kernel = SDM_KERNEL_GOLOVIN;
+    cfg->precision = SDM_PREC_FP64;
+    cfg->golovin_b = 1.5e3;
+    cfg->dt = 1.0;
+    cfg->dv = 1.0e6;
+    cfg->ry_k1 = 1.19e8;
+    cfg->ry_k2 = 8.0e3;
+    cfg->ry_k3 = 201.0;
+    cfg->ry_r1 = 40.0e-6;
+    cfg->ry_r2 = 600.0e-6;
+    cfg->n_cells = 1;
+}
+
+int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t largest_cell)
+{
+    const int64_t slots = capacity_sd + n_cells;
+    int64_t bytes = slots * (8 + 8 + 4) + ((int64_t)n_cells + 1) * 4 + (int64_t)sizeof(InstDev);
+    if (largest_cell > kSmemMaxCell) {
+        // big-cell scratch, at most: keys, ranks, perm per SD; counts per chunk and bucket
+        const int lb = big_lb(largest_cell);
+        const int64_t chunks = (capacity_sd + kBigChunk - 1) / kBigChunk + n_cells;
+        bytes += capacity_sd * (8 + 4 + 4) + (chunks << lb) * 4 + ((int64_t)n_cells << lb) * 4;
+    }
+    return bytes;
+}
+
+sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_stream, sdm_ctx **out)
+{
+    if (!out)
+        return fail(nullptr, SDM_EINVAL, "out is NULL");
+    sdm_status st = check_config(cfg, nullptr);
+    if (st != SDM_OK)
+        return st;
+    if (capacity_sd < 1 || capacity_sd + cfg->n_cells > (int64_t)INT32_MAX)
+        return fail(nullptr, SDM_EINVAL, "capacity_sd must be in [1, 2^31 - 1 - n_cells]");
+    sdm_ctx *c = new (std::nothrow) sdm_ctx();
+    if (!c)
+        return fail(nullptr, SDM_ENOMEM, "host allocation failed");
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->mem.fn = cfg->alloc;
+    c->mem.ffn = cfg->free;
+    c->mem.user = cfg->alloc_user;
+    c->mem.stream = c->stream;
+    c->capacity_sd = capacity_sd;
+    c->n_slots_cap = capacity_sd + cfg->n_cells;
+    c->step = cfg->step0;
+    c->d_xi = (int64_t *)c->mem.get(sizeof(int64_t) * c->n_slots_cap);
+    c->d_v = (double *)c->mem.get(sizeof(double) * c->n_slots_cap);
+    c->d_id_of_slot = (int32_t *)c->mem.get(sizeof(int32_t) * c->n_slots_cap);
+    c->d_cell_off = (int32_t *)c->mem.get(sizeof(int32_t) * (cfg->n_cells + 1));
+    c->d_inst = (InstDev *)c->mem.get(sizeof(InstDev));
+    c->device_bytes = c->n_slots_cap * 20 + (int64_t)(cfg->n_cells + 1) * 4 + (int64_t)sizeof(InstDev);
+    if (!c->d_xi || !c->d_v || !c->d_id_of_slot || !c->d_cell_off || !c->d_inst) {
+        sdm_destroy(c);
+        return fail(nullptr, SDM_ENOMEM, "device allocation of %lld SDs failed", (long long)capacity_sd);
+    }
+    *out = c;
+    return SDM_OK;
+}
+
+sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, const double *volume,
+                              const int32_t *cell_id, int on_device)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (n_sd < 1 || n_sd > ctx->capacity_sd)
+        return fail(&ctx->error, SDM_EINVAL, "n_sd = %lld outside [1, capacity_sd = %lld]", (long long)n_sd,
+                    (long long)ctx->capacity_sd);
+    if (!xi || !volume || !cell_id)
+        return fail(&ctx->error, SDM_EINVAL, "xi, volume and cell_id are required");
+    const int32_t n_cells = ctx->cfg.n_cells;
+    cudaStream_t s = ctx->stream;
+    DevMem &mem = ctx->mem;
+    // staging of host inputs
+    const size_t b_xi = sizeof(int64_t) * n_sd, b_v = sizeof(double) * n_sd, b_c = sizeof(int32_t) * n_sd;
+    void *stage = nullptr;
+    const int64_t *dxi = xi;
+    const double *dv = volume;
+    const int32_t *dcell = cell_id;
+    const size_t b_stage = b_xi + b_v + b_c;
+    if (!on_device) {
+        stage = mem.get(b_stage);
+        if (!stage)
+            return fail(&ctx->error, SDM_ENOMEM, "staging allocation failed");
+        char *p = (char *)stage;
+        CTX_CUDA(ctx, cudaMemcpyAsync(p, xi, b_xi, cudaMemcpyHostToDevice, s));
+        CTX_CUDA(ctx, cudaMemcpyAsync(p + b_xi, volume, b_v, cudaMemcpyHostToDevice, s));
+        CTX_CUDA(ctx, cudaMemcpyAsync(p + b_xi + b_v, cell_id, b_c, cudaMemcpyHostToDevice, s));
+        dxi = (const int64_t *)p;
+        dv = (const double *)(p + b_xi);
+        dcell = (const int32_t *)(p + b_xi + b_v);
+    }
+    // counts, flags, first bad index
+    const size_t b_counts = sizeof(uint32_t) * n_cells + 16;
+    void *meta = mem.get(b_counts);
+    if (!meta) {
+        mem.put(stage, b_stage);
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    }
+    uint32_t *d_counts = (uint32_t *)meta;
+    uint32_t *d_flags = d_counts + n_cells;
+    unsigned long long *d_bad = (unsigned long long *)(((uintptr_t)(d_flags + 1) + 7) & ~(uintptr_t)7);
+    // d_bad lies inside the 16 spare bytes after the counts
+    CTX_CUDA(ctx, cudaMemsetAsync(meta, 0, b_counts, s));
+    CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
+    validate_count_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_counts, d_flags, d_bad);
+    std::vector<uint32_t> counts(n_cells);
+    uint32_t flags = 0;
+    unsigned long long bad = 0;
+    CTX_CUDA(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * n_cells, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(&flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    if (flags & 1u) {
+        mem.put(meta, b_counts);
+        mem.put(stage, b_stage);
+        return fail(&ctx->error, SDM_EINVAL,
+                    "SD %llu: need xi >= 0, volume in [1e-30, 1e30] m^3, cell in [0, %d)", bad, n_cells);
+    }
+    // padded layout: every cell starts at an even slot
+    std::vector<int32_t> poff(n_cells + 1), uoff(n_cells + 1);
+    int64_t ps = 0, us = 0;
+    int32_t largest = 0;
+    for (int32_t c = 0; c < n_cells; ++c) {
+        poff[c] = (int32_t)ps;
+        uoff[c] = (int32_t)us;
+        ps += (counts[c] + 1) & ~1u;
+        us += counts[c];
+        largest = std::max<int32_t>(largest, (int32_t)counts[c]);
+    }
+    poff[n_cells] = (int32_t)ps;
+    uoff[n_cells] = (int32_t)us;
+    // slot positions for unsorted input (stable by id)
+    std::vector<int32_t> pos;
+    if (flags & 2u) {
+        std::vector<int32_t> hcell(n_sd);
+        if (on_device) {
+            CTX_CUDA(ctx, cudaMemcpyAsync(hcell.data(), cell_id, b_c, cudaMemcpyDeviceToHost, s));
+            CTX_CUDA(ctx, cudaStreamSynchronize(s));
+        } else {
+            std::memcpy(hcell.data(), cell_id, b_c);
+        }
+        pos.resize(n_sd);
+        std::vector<int32_t> fill(poff.begin(), poff.end() - 1);
+        for (int64_t i = 0; i < n_sd; ++i)
+            pos[i] = fill[hcell[i]]++;
+    }
+    const size_t b_aux = sizeof(int32_t) * 2 * (n_cells + 1) + (pos.empty() ? 0 : b_c);
+    void *aux = mem.get(b_aux);
+    if (!aux) {
+        mem.put(meta, b_counts);
+        mem.put(stage, b_stage);
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    }
+    int32_t *d_poff = (int32_t *)aux;
+    int32_t *d_uoff = d_poff + (n_cells + 1);
+    int32_t *d_pos = pos.empty() ? nullptr : d_uoff + (n_cells + 1);
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_poff, poff.data(), sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_uoff, uoff.data(), sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
+    if (d_pos)
+        CTX_CUDA(ctx, cudaMemcpyAsync(d_pos, pos.data(), b_c, cudaMemcpyHostToDevice, s));
+    fill_padding_kernel<<<1216, 256, 0, s>>>(ps, ctx->d_xi, ctx->d_v, ctx->d_id_of_slot);
+    scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
+                                        ctx->d_id_of_slot);
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff.data(), sizeof(int32_t) * (n_cells + 1),
+                                  cudaMemcpyHostToDevice, s));
+    ctx->n_sd = n_sd;
+    ctx->n_slots = ps;
+    ctx->largest_cell = largest;
+    ctx->h_cell_off = poff;
+    ctx->dev_base = ctx->step;
+    InstDev inst = make_inst(ctx);
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
+    CTX_CUDA(ctx, cudaGetLastError());
+    CTX_CUDA(ctx, cudaStreamSynchronize(s)); // host vectors above go out of scope
+    mem.put(aux, b_aux);
+    mem.put(meta, b_counts);
+    mem.put(stage, b_stage);
+    ctx->has_attributes = true;
+    if (ctx->self_batch) {
+        batch_release(ctx->self_batch);
+        delete ctx->self_batch;
+        ctx->self_batch = nullptr;
+    }
+    return SDM_OK;
+}
+
+sdm_status sdm_coalescence_step(sdm_ctx *ctx, int32_t n_steps)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_attributes has not been called");
+    if (n_steps < 0)
+        return fail(&ctx->error, SDM_EINVAL, "n_steps < 0");
+    if (!ctx->self_batch) {
+        sdm_batch *b = new (std::nothrow) sdm_batch();
+        if (!b)
+            return fail(&ctx->error, SDM_ENOMEM, "host allocation failed");
+        sdm_ctx *one[1] = {ctx};
+        st = batch_init(b, one, 1, ctx->stream, 0, 0);
+        if (st != SDM_OK) {
+            ctx->error = b->error;
+            batch_release(b);
+            delete b;
+            return st;
+        }
+        ctx->self_batch = b;
+    }
+    st = batch_step(ctx->self_batch, n_steps);
+    if (st != SDM_OK)
+        ctx->error = ctx->self_batch->error;
+    return st;
+}
+
+sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, int per_cell, double *out,
+                        int out_on_device)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_attributes has not been called");
+    if (!r_edges || !out || n_edges < 2 || n_edges > kMaxEdges)
+        return fail(&ctx->error, SDM_EINVAL, "need r_edges, out and 2 <= n_edges <= %d", kMaxEdges);
+    for (int32_t i = 0; i + 1 < n_edges; ++i)
+        if (!(r_edges[i] > 0.0) || !(r_edges[i + 1] > r_edges[i]) || !std::isfinite(r_edges[i + 1]))
+            return fail(&ctx->error, SDM_EINVAL, "r_edges must be finite, > 0 and strictly increasing");
+    const int32_t nb = n_edges - 1;
+    const int64_t n_out = per_cell ? (int64_t)ctx->cfg.n_cells * nb : nb;
+    cudaStream_t s = ctx->stream;
+    const size_t b_edges = sizeof(double) * n_edges, b_acc = sizeof(double) * n_out;
+    const size_t b_tmp = b_edges + 2 * b_acc;
+    char *tmp = (char *)ctx->mem.get(b_tmp);
+    if (!tmp)
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    double *d_edges = (double *)tmp;
+    double *d_acc = (double *)(tmp + b_edges);
+    double *d_out = out_on_device ? out : (double *)(tmp + b_edges + b_acc);
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, r_edges, b_edges, cudaMemcpyHostToDevice, s));
+    CTX_CUDA(ctx, cudaMemsetAsync(d_acc, 0, b_acc, s));
+    spectrum_kernel<<<ctx->cfg.n_cells, kSpecNT, 0, s>>>(ctx->d_inst, d_edges, n_edges, per_cell ? 1 : 0, d_acc);
+    const double vol = per_cell ? ctx->cfg.dv : ctx->cfg.dv * (double)ctx->cfg.n_cells;
+    spectrum_finalize_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(d_acc, d_edges, n_edges, n_out, vol, d_out);
+    CTX_CUDA(ctx, cudaGetLastError());
+    if (!out_on_device) {
+        CTX_CUDA(ctx, cudaMemcpyAsync(out, d_out, b_acc, cudaMemcpyDeviceToHost, s));
+        CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    ctx->mem.put(tmp, b_tmp);
+    return SDM_OK;
+}
+
+sdm_status sdm_get_attributes(sdm_ctx *ctx, int64_t *xi, double *volume, int on_device)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_attributes has not been called");
+    if (!xi && !volume)
+        return SDM_OK;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = ctx->n_sd;
+    if (on_device) {
+        gather_kernel<<<1216, 256, 0, s>>>(ctx->n_slots, ctx->d_xi, ctx->d_v, ctx->d_id_of_slot, xi, volume);
+        CTX_CUDA(ctx, cudaGetLastError());
+        return SDM_OK;
+    }
+    const size_t bx = sizeof(int64_t) * n, bv = sizeof(double) * n;
+    char *tmp = (char *)ctx->mem.get(bx + bv);
+    if (!tmp)
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    gather_kernel<<<1216, 256, 0, s>>>(ctx->n_slots, ctx->d_xi, ctx->d_v, ctx->d_id_of_slot,
+                                       xi ? (int64_t *)tmp : nullptr, volume ? (double *)(tmp + bx) : nullptr);
+    CTX_CUDA(ctx, cudaGetLastError());
+    if (xi)
+        CTX_CUDA(ctx, cudaMemcpyAsync(xi, tmp, bx, cudaMemcpyDeviceToHost, s));
+    if (volume)
+        CTX_CUDA(ctx, cudaMemcpyAsync(volume, tmp + bx, bv, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->mem.put(tmp, bx + bv);
+    return SDM_OK;
+}
+
+sdm_status sdm_get_info(const sdm_ctx *ctx, sdm_info *out)
+{
+    if (!ctx || !out)
+        return fail(nullptr, SDM_EINVAL, "context and out are required");
+    out->n_sd = ctx->n_sd;
+    out->capacity_sd = ctx->capacity_sd;
+    out->step = ctx->step;
+    out->device_bytes = ctx->device_bytes + (ctx->self_batch ? ctx->self_batch->plan.bytes : 0);
+    out->n_cells = ctx->cfg.n_cells;
+    out->largest_cell = ctx->largest_cell;
+    return SDM_OK;
+}
+
+sdm_status sdm_destroy(sdm_ctx *ctx)
+{
+    if (!ctx)
+        return SDM_OK;
+    if (ctx->self_batch) {
+        batch_release(ctx->self_batch);
+        delete ctx->self_batch;
+    }
+    ctx->mem.put(ctx->d_xi, 0);
+    ctx->mem.put(ctx->d_v, 0);
+    ctx->mem.put(ctx->d_id_of_slot, 0);
+    ctx->mem.put(ctx->d_cell_off, 0);
+    ctx->mem.put(ctx->d_inst, 0);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    delete ctx;
+    if (e != cudaSuccess)
+        return fail(nullptr, SDM_ECUDA, "sdm_destroy: %s", cudaGetErrorString(e));
+    return SDM_OK;
+}
+
+const char *sdm_last_error(const sdm_ctx *ctx)
+{
+    if (ctx)
+        return ctx->error.c_str();
+    return g_thread_error.c_str();
+}
+
+sdm_status sdm_batch_create(sdm_ctx *const *ctxs, int32_t n_ctx, void *cuda_stream, int32_t use_graph,
+                            int32_t graph_steps, sdm_batch **out)
+{
+    if (!out || !ctxs || n_ctx < 1)
+        return fail(nullptr, SDM_EINVAL, "need out, ctxs and n_ctx >= 1");
+    sdm_batch *b = new (std::nothrow) sdm_batch();
+    if (!b)
+        return fail(nullptr, SDM_ENOMEM, "host allocation failed");
+    sdm_status st = batch_init(b, ctxs, n_ctx, (cudaStream_t)cuda_stream, use_graph, graph_steps);
+    if (st != SDM_OK) {
+        g_thread_error = b->error;
+        batch_release(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return SDM_OK;
+}
+
+sdm_status sdm_batch_step(sdm_batch *batch, int32_t n_steps)
+{
+    if (!batch)
+        return fail(nullptr, SDM_EINVAL, "batch is NULL");
+    return batch_step(batch, n_steps);
+}
+
+sdm_status sdm_batch_destroy(sdm_batch *batch)
+{
+    if (!batch)
+        return SDM_OK;
+    batch_release(batch);
+    cudaError_t e = cudaStreamSynchronize(batch->stream);
+    delete batch;
+    if (e != cudaSuccess)
+        return fail(nullptr, SDM_ECUDA, "sdm_batch_destroy: %s", cudaGetErrorString(e));
+    return SDM_OK;
+}
+
+const char *sdm_batch_last_error(const sdm_batch *batch)
+{
+    if (batch)
+        return batch->error.c_str();
+    return g_thread_error.c_str();
+}
+
+} // extern "C"

@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: the library builds and loads, exports every
+function include/sdm.h declares, and its host-only calls behave."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_17238_gb300 import build as B
+    from paper_2103_17238_gb300 import sdm
+
+    B.build()
+    return sdm.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sdm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(sdm_[a-z_]+)\s*\(", src))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2103_17238_gb300 import sdm
+
+    names = _declared()
+    assert "sdm_create" in names and "sdm_coalescence_step" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(sdm.EXPORTS)
+
+
+def test_config_default_is_the_paper_example(lib):
+    from paper_2103_17238_gb300 import sdm
+
+    c = sdm.sdm_config_default()
+    assert (c.kernel, c.precision, c.golovin_b, c.dt, c.dv, c.n_cells) == (0, 0, 1500.0, 1.0, 1e6, 1)
+    assert (c.ry_k1, c.ry_k2, c.ry_k3, c.ry_r1, c.ry_r2) == (1.19e8, 8e3, 201.0, 40e-6, 600e-6)
+
+
+def test_ctypes_layout_matches_the_header(tmp_path):
+    """Field offsets of the Python structures equal the C compiler's."""
+    from paper_2103_17238_gb300 import sdm
+
+    prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "sdm.h"', 'int main(void){']
+    for st in (sdm.sdm_config, sdm.sdm_info):
+        name = st.__name__
+        prog.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            prog.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    prog.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(prog))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for st in (sdm.sdm_config, sdm.sdm_info):
+        assert int(out[st.__name__]) == ctypes.sizeof(st)
+        for f, _ in st._fields_:
+            assert int(out[f"{st.__name__}.{f}"]) == getattr(st, f).offset, f
+
+
+@pytest.mark.parametrize("field,value", [("dt", 0.0), ("dv", -1.0), ("kernel", 7), ("precision", 3),
+                                         ("n_cells", 0), ("ry_r2", 1e-6), ("golovin_b", float("nan"))])
+def test_create_rejects_bad_config_before_touching_the_gpu(lib, field, value):
+    from paper_2103_17238_gb300 import sdm
+
+    c = sdm.sdm_config_default()
+    setattr(c, field, value)
+    with pytest.raises(sdm.SdmError) as e:
+        sdm.sdm_create(c, 16, 0)
+    assert e.value.status == sdm.SDM_EINVAL
+    assert lib.sdm_last_error(None)
+
+
+def test_destroy_null_and_footprint(lib):
+    from paper_2103_17238_gb300 import sdm
+
+    assert lib.sdm_destroy(None) == sdm.SDM_OK
+    assert lib.sdm_batch_destroy(None) == sdm.SDM_OK
+    small = sdm.sdm_footprint_bytes(4096, 1, 4096)
+    assert small == (4096 + 1) * 20 + 2 * 4 + sdm.sdm_footprint_bytes(0, 1, 0) - (1 * 20 + 2 * 4)
+    big = sdm.sdm_footprint_bytes(2**20, 1, 2**20)
+    assert big > 2**20 * 20 + 2**20 * 16
