@@ -31,7 +31,8 @@ struct InstDev {
     double b;                // Golovin constant
     double k1, k2, k3, r1, r2;
     float bf, k1f, k2f, k3f, r1f, r2f; // binary32 roundings of the above
-    int32_t kernel, precision, n_cells, pad_;
+    int32_t kernel, precision, n_cells;
+    uint32_t status; // bit 0: a bounded device wait gave up (reported as SDM_ETIMEOUT)
 };
 
 struct WorkItem {
@@ -75,8 +76,40 @@ __device__ __forceinline__ double uniform53(uint32_t wa, uint32_t wb)
     return __dmul_rn(__ull2double_rn(m), 0x1p-53);
 }
 
-// A binary32 lower bound of the same uniform: its top 24 bits, exactly.
-__device__ __forceinline__ float uniform_lo24(uint32_t wa) { return __uint2float_rn(wa >> 8) * 0x1p-24f; }
+// A binary32 lower bound of the same uniform: its top 23 bits, exactly
+// ((wa >> 9) 2^-23 built as a float in [1, 2) minus 1).
+__device__ __forceinline__ float uniform_lo23(uint32_t wa) { return __uint_as_float(0x3F800000u | (wa >> 9)) - 1.0f; }
+
+// ------------------------------------------------------------ conversions
+// Blackwell Ultra issues F2F.F64 and I2F.S64 on its narrow binary64 pipe, so
+// the common path converts with integer operations instead.  Both are
+// exactly round-to-nearest-even, like (float)x in C.
+
+// x in the normal binary32 range (in_range reports it); sign kept.
+__device__ __forceinline__ float d2f_rn(double x, bool &in_range)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    in_range = (e - 897u) < 253u; // binary32 exponent field 1 .. 253 before rounding
+    const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const uint32_t rest = lo & 0x1FFFFFFFu;
+    uint32_t bits = ((e - 896u) << 23) + m;
+    bits += (uint32_t)(rest > 0x10000000u) | ((uint32_t)(rest == 0x10000000u) & (m & 1u));
+    return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
+// two exact 16-bit halves, one rounding in the final fused add
+__device__ __forceinline__ float u32_to_f32_rn(uint32_t u)
+{
+    const float lo = __uint_as_float((u & 0xFFFFu) | 0x4B000000u) - 8388608.0f;
+    const float hi = __uint_as_float((u >> 16) | 0x4B000000u) - 8388608.0f;
+    return __fmaf_rn(hi, 65536.0f, lo);
+}
+
+__device__ __forceinline__ float xi_to_f32_rn(int64_t x)
+{
+    return ((uint64_t)x >> 32) == 0 ? u32_to_f32_rn((uint32_t)x) : __ll2float_rn(x);
+}
 
 // ------------------------------------------------------------- cube root
 // The library's cube root is a fixed sequence of IEEE operations so that its
@@ -177,15 +210,6 @@ __device__ __forceinline__ double vt_exact(const InstDev &P, double r)
     return __dmul_rn(P.k3, __dsqrt_rn(r));
 }
 
-__device__ __forceinline__ float vt32(const InstDev &P, float r)
-{
-    if (r < P.r1f)
-        return __fmul_rn(P.k1f, __fmul_rn(r, r));
-    if (r < P.r2f)
-        return __fmul_rn(P.k2f, r);
-    return __fmul_rn(P.k3f, __fsqrt_rn(r));
-}
-
 // --------------------------------------------------------------- p and gamma
 // Exact binary64 probability (the definition).
 __device__ __noinline__ double probability_exact(const InstDev &P, double scale, int64_t xi_j, double vj,
@@ -215,6 +239,44 @@ __device__ __forceinline__ int64_t gamma_exact(double p, double u, int64_t xi_j,
     return __double2ll_rz(g);
 }
 
+// Per-run constants of the pair arithmetic, loaded once per cell.
+struct PairConsts {
+    float bf, k1f, k2f, k3f, r1f, r2f;
+    int32_t kernel, precision;
+};
+
+__device__ __forceinline__ PairConsts pair_consts(const InstDev *P)
+{
+    PairConsts c;
+    c.bf = P->bf;
+    c.k1f = P->k1f;
+    c.k2f = P->k2f;
+    c.k3f = P->k3f;
+    c.r1f = P->r1f;
+    c.r2f = P->r2f;
+    c.kernel = P->kernel;
+    c.precision = P->precision;
+    return c;
+}
+
+__device__ __forceinline__ float vt32c(const PairConsts &C, float r)
+{
+    if (r < C.r1f)
+        return __fmul_rn(C.k1f, __fmul_rn(r, r));
+    if (r < C.r2f)
+        return __fmul_rn(C.k2f, r);
+    return __fmul_rn(C.k3f, __fsqrt_rn(r));
+}
+
+// The rare exact path: the binary64 definition (FP64 mode) or the widened
+// binary32 value (KFP32 mode), then gamma.
+__device__ __noinline__ int64_t gamma_slow(const InstDev *P, double scale, float pf, int64_t xi_j, int64_t xi_k,
+                                           double vj, double vk, uint32_t wa, uint32_t wb)
+{
+    const double p = P->precision == PREC_KFP32 ? (double)pf : probability_exact(*P, scale, xi_j, vj, vk);
+    return gamma_exact(p, uniform53(wa, wb), xi_j, xi_k);
+}
+
 // Collision count of one pair (xi_j >= xi_k > 0).  The binary32 stage is
 // itself the definition in KFP32 mode; in FP64 mode it is a filter: with
 // pf the binary32 value and M a binary32 magnitude of every term of p,
@@ -222,41 +284,43 @@ __device__ __forceinline__ int64_t gamma_exact(double p, double u, int64_t xi_j,
 // within 1 ulp), so pf + 2^-12 M + 2^-100 < u implies p < u, i.e. gamma = 0.
 // Near a terminal-velocity regime boundary, or when a binary32 value leaves
 // the normal range, the filter abstains and the exact path decides.
-__device__ __forceinline__ int64_t pair_gamma(const InstDev &P, double scale, float scale_f, int64_t xi_j,
-                                              int64_t xi_k, double vj, double vk, uint32_t wa, uint32_t wb)
+__device__ __forceinline__ int64_t pair_gamma(const InstDev *P, const PairConsts &C, double scale, float scale_f,
+                                              int64_t xi_j, int64_t xi_k, double vj, double vk, uint32_t wa,
+                                              uint32_t wb)
 {
-    const float u_lo = uniform_lo24(wa);
-    const float vjf = __double2float_rn(vj), vkf = __double2float_rn(vk);
-    const float xjf = __ll2float_rn(xi_j);
+    const float u_lo = uniform_lo23(wa);
+    bool in_j, in_k;
+    const float vjf = d2f_rn(vj, in_j), vkf = d2f_rn(vk, in_k);
+    const float xjf = xi_to_f32_rn(xi_j);
     float pf, mag;
-    bool ok;
-    if (P.kernel == KERNEL_GOLOVIN) {
-        const float K = __fmul_rn(P.bf, __fadd_rn(vjf, vkf));
+    bool ok = in_j & in_k;
+    if (C.kernel == KERNEL_GOLOVIN) {
+        const float K = __fmul_rn(C.bf, __fadd_rn(vjf, vkf));
         pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
         mag = pf;
-        ok = K >= 0x1p-126f;
+        ok &= K >= 0x1p-126f;
     } else {
         const float rj = radius32(vjf), rk = radius32(vkf);
-        const float tj = vt32(P, rj), tk = vt32(P, rk);
+        const float tj = vt32c(C, rj), tk = vt32c(C, rk);
         const float s = __fadd_rn(rj, rk);
         const float a = __fmul_rn(kPiF, __fmul_rn(s, s));
         const float K = __fmul_rn(a, fabsf(__fsub_rn(tj, tk)));
         pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
         const float km = a * (tj + tk);
         mag = (km * xjf) * scale_f;
-        const float g1 = P.r1f * 0x1p-16f, g2 = P.r2f * 0x1p-16f;
-        ok = km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f) && fabsf(rj - P.r1f) > g1 &&
-             fabsf(rk - P.r1f) > g1 && fabsf(rj - P.r2f) > g2 && fabsf(rk - P.r2f) > g2;
+        const float g1 = C.r1f * 0x1p-16f, g2 = C.r2f * 0x1p-16f;
+        ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f) && fabsf(rj - C.r1f) > g1 &&
+              fabsf(rk - C.r1f) > g1 && fabsf(rj - C.r2f) > g2 && fabsf(rk - C.r2f) > g2;
     }
-    if (P.precision == PREC_KFP32) {
-        if (pf < u_lo)
+    if (C.precision == PREC_KFP32) {
+        if (ok && pf < u_lo)
             return 0;
-        return gamma_exact((double)pf, uniform53(wa, wb), xi_j, xi_k);
+    } else {
+        const float p_hi = pf + mag * 0x1p-12f + 0x1p-100f;
+        if (ok && p_hi < u_lo)
+            return 0;
     }
-    const float p_hi = pf + mag * 0x1p-12f + 0x1p-100f;
-    if (ok && p_hi < u_lo)
-        return 0;
-    return gamma_exact(probability_exact(P, scale, xi_j, vj, vk), uniform53(wa, wb), xi_j, xi_k);
+    return gamma_slow(P, scale, pf, xi_j, xi_k, vj, vk, wa, wb);
 }
 
 // Shima update for gamma > 0.  Returns true when the j SD's volume changed
@@ -278,11 +342,13 @@ __device__ __forceinline__ bool shima_update(int64_t gamma, int64_t &xi_j, int64
     return true;
 }
 
-// dt/dV [n_c (n_c - 1) / 2] / floor(n_c / 2), once per cell.
+// dt/dV [n_c (n_c - 1) / 2] / floor(n_c / 2), once per cell.  The ratio is
+// exactly n_c - 1 for even n_c and n_c for odd n_c, so the IEEE quotient of
+// the definition equals that integer and no division is needed.
 __device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
 {
-    const double ratio = __ddiv_rn(__ll2double_rn(n_c * (n_c - 1) / 2), __ll2double_rn(n_c / 2));
-    return __dmul_rn(dtdv, ratio);
+    const int64_t ratio = (n_c & 1) ? n_c : n_c - 1;
+    return __dmul_rn(dtdv, __ll2double_rn(ratio));
 }
 
 } // namespace sdm

@@ -76,15 +76,65 @@ __device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ra, uint64_t kb, 
     return (ka < kb) | ((ka == kb) & (ra < rb));
 }
 
+// ------------------------------------------------- bulk copies, mbarriers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Global -> shared bulk copy through the TMA engine, completing on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase: ~2^22 polls (each poll may suspend the
+// thread for a hardware-defined interval), then give up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 22); ++it)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+
 // -------------------------------------------------------------- cell step
-template <int CAP>
+template <int CAP, int STAGES>
 struct CellSmem {
-    static constexpr size_t bytes = (size_t)CAP * (8 + 8 + 8 + 4 + 2 + 2);
+    // STAGES x (xi, v) staging + key, bucket, rank, perm work arrays
+    static constexpr size_t bytes = (size_t)CAP * (16 * STAGES + 8 + 4 + 2 + 2);
 };
 
-template <int CAP, int NT>
-__global__ void __launch_bounds__(NT) cell_step_kernel(const WorkItem *__restrict__ items,
-                                                       const InstDev *const *__restrict__ insts, int64_t step_offset)
+// Persistent: CTA b handles work items b, b + gridDim.x, ...  Thread 0
+// streams the next STAGES - 1 cells into shared memory with bulk copies
+// while the CTA works on the current one.
+template <int CAP, int NT, int STAGES>
+__global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
+                                                       InstDev *const *__restrict__ insts, int64_t step_offset)
 {
     constexpr int NB = CAP;
     constexpr int LB = ilog2_c(CAP);
@@ -92,137 +142,176 @@ __global__ void __launch_bounds__(NT) cell_step_kernel(const WorkItem *__restric
     static_assert((1 << LB) == CAP, "CAP must be a power of two");
     static_assert(CAP <= 65536, "ranks are stored in 16 bits");
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    int64_t *s_xi = reinterpret_cast<int64_t *>(smem_raw);
-    double *s_v = reinterpret_cast<double *>(s_xi + CAP);
-    uint64_t *s_key = reinterpret_cast<uint64_t *>(s_v + CAP);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int64_t *st_xi = reinterpret_cast<int64_t *>(smem_raw);          // [STAGES][CAP]
+    double *st_v = reinterpret_cast<double *>(st_xi + STAGES * CAP); // [STAGES][CAP]
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(st_v + STAGES * CAP);
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_key + CAP);
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + NB);
     uint16_t *s_perm = s_rank + CAP;
+    __shared__ uint64_t s_bar[STAGES];
+    __shared__ int4 s_meta[STAGES]; // off, n, cell, inst
     __shared__ uint32_t s_warp[32];
     __shared__ double s_scale;
     __shared__ float s_scale_f;
 
-    const WorkItem it = items[blockIdx.x];
-    const InstDev *__restrict__ P = insts[it.inst];
-    const int32_t off = P->cell_off[it.cell];
-    const int n = P->cell_off[it.cell + 1] - off; // even, <= CAP
-    const int64_t s = P->step + step_offset;
-    const uint64_t seed = P->seed;
-    int64_t *__restrict__ gxi = P->xi + off;
-    double *__restrict__ gv = P->v + off;
     const int t = threadIdx.x;
-
-    // 1. state into shared memory (16-byte vectors; every cell starts at an even slot)
-    for (int i = t; i < n / 2; i += NT) {
-        const longlong2 a = reinterpret_cast<const longlong2 *>(gxi)[i];
-        const double2 b = reinterpret_cast<const double2 *>(gv)[i];
-        s_xi[2 * i] = a.x;
-        s_xi[2 * i + 1] = a.y;
-        s_v[2 * i] = b.x;
-        s_v[2 * i + 1] = b.y;
-    }
-    for (int i = t; i < NB; i += NT)
-        s_hist[i] = 0u;
-    __syncthreads();
-
-    // 2. sort keys of live SDs and their bucket slots
-    uint64_t key[2 * RP];
-    uint32_t slot[2 * RP];
-#pragma unroll
-    for (int r = 0; r < RP; ++r) {
-        const int q = t + r * NT;
-        slot[2 * r] = 0xFFFFFFFFu;
-        slot[2 * r + 1] = 0xFFFFFFFFu;
-        key[2 * r] = 0;
-        key[2 * r + 1] = 0;
-        if (2 * q < n) {
-            const bool la = s_xi[2 * q] > 0, lb = s_xi[2 * q + 1] > 0;
-            if (la | lb) {
-                const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)it.cell, s, 0u);
-                if (la) {
-                    key[2 * r] = ((uint64_t)w.x << 32) | w.y;
-                    slot[2 * r] = atomicAdd(&s_hist[key[2 * r] >> (64 - LB)], 1u);
-                }
-                if (lb) {
-                    key[2 * r + 1] = ((uint64_t)w.z << 32) | w.w;
-                    slot[2 * r + 1] = atomicAdd(&s_hist[key[2 * r + 1] >> (64 - LB)], 1u);
-                }
-            }
-        }
-    }
-    __syncthreads();
-
-    // 3. bucket starts; the total is the live count n_c
-    const uint32_t n_c = block_exclusive_scan<NT, NB>(s_hist, s_warp);
-    if (n_c < 2)
-        return;
     if (t == 0) {
-        const double sc = cell_scale(P->dtdv, (int64_t)n_c);
-        s_scale = sc;
-        s_scale_f = __double2float_rn(sc);
-    }
-
-    // 4. scatter into bucket order
-#pragma unroll
-    for (int r = 0; r < RP; ++r) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (slot[2 * r + h] != 0xFFFFFFFFu) {
-                const uint32_t pos = s_hist[key[2 * r + h] >> (64 - LB)] + slot[2 * r + h];
-                s_key[pos] = key[2 * r + h];
-                s_rank[pos] = (uint16_t)(2 * (t + r * NT) + h);
-            }
-        }
+        for (int i = 0; i < STAGES; ++i)
+            mbar_init(&s_bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // 5. order within each bucket by (key, rank)
-    for (uint32_t pos = t; pos < n_c; pos += NT) {
-        const uint64_t k = s_key[pos];
-        const uint32_t rk = s_rank[pos];
-        const uint32_t b = (uint32_t)(k >> (64 - LB));
-        const uint32_t lo = s_hist[b];
-        const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
-        uint32_t cnt = 0;
-        for (uint32_t m = lo; m < hi; ++m)
-            cnt += key_less(s_key[m], s_rank[m], k, rk) ? 1u : 0u;
-        s_perm[lo + cnt] = (uint16_t)rk;
-    }
-    __syncthreads();
+    auto issue = [&](int k) { // thread 0: start loading the k-th cell of this CTA
+        const int i = blockIdx.x + k * gridDim.x;
+        if (i >= n_items)
+            return;
+        const int sg = k % STAGES;
+        const WorkItem it = items[i];
+        const InstDev *P = insts[it.inst];
+        const int32_t off = P->cell_off[it.cell];
+        const int32_t n = P->cell_off[it.cell + 1] - off;
+        s_meta[sg] = make_int4(off, n, it.cell, it.inst);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)n * 16u);
+        bulk_g2s(st_xi + sg * CAP, P->xi + off, (uint32_t)n * 8u, &s_bar[sg]);
+        bulk_g2s(st_v + sg * CAP, P->v + off, (uint32_t)n * 8u, &s_bar[sg]);
+    };
+    if (t == 0)
+        for (int k = 0; k < STAGES - 1; ++k)
+            issue(k);
 
-    // 6. pairs (l = 2q, 2q + 1 share one Philox block)
-    const uint32_t n_pairs = n_c / 2;
-    const double scale = s_scale;
-    const float scale_f = s_scale_f;
-    for (uint32_t q = t; 2 * q < n_pairs; q += NT) {
-        const uint4 w = draw4(seed, q, (uint32_t)it.cell, s, 1u);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t l = 2 * q + h;
-            if (l >= n_pairs)
-                break;
-            int a = s_perm[2 * l], b = s_perm[2 * l + 1];
-            int64_t xa = s_xi[a], xb = s_xi[b];
-            if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
-                const int tmp = a;
-                a = b;
-                b = tmp;
-                const int64_t tx = xa;
-                xa = xb;
-                xb = tx;
+    for (int k = 0; blockIdx.x + k * gridDim.x < n_items; ++k) {
+        if (t == 0)
+            issue(k + STAGES - 1);
+        const int sg = k % STAGES;
+        const bool arrived = mbar_wait_bounded(&s_bar[sg], (uint32_t)(k / STAGES) & 1u);
+        if (!__syncthreads_and(arrived)) {
+            // a copy never completed: report, wait (bounded) for the copies
+            // still in flight, leave
+            if (t == 0) {
+                atomicOr(&insts[s_meta[sg].w]->status, 1u);
+                for (int kk = k; kk < k + STAGES; ++kk) // copies issued and not consumed
+                    if (blockIdx.x + kk * gridDim.x < n_items)
+                        mbar_wait_bounded(&s_bar[kk % STAGES], (uint32_t)(kk / STAGES) & 1u);
             }
-            double va = s_v[a], vb = s_v[b];
-            const int64_t g = pair_gamma(*P, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
-            if (g > 0) {
-                const bool split = shima_update(g, xa, xb, va, vb);
-                gxi[a] = xa;
-                gxi[b] = xb;
-                gv[b] = vb;
-                if (split)
-                    gv[a] = va;
+            return;
+        }
+        const int4 meta = s_meta[sg];
+        const int n = meta.y;
+        const uint32_t cell = (uint32_t)meta.z;
+        InstDev *__restrict__ P = insts[meta.w];
+        const int64_t s = P->step + step_offset;
+        const uint64_t seed = P->seed;
+        const int64_t *xs = st_xi + sg * CAP;
+        const double *vs = st_v + sg * CAP;
+        int64_t *__restrict__ gxi = P->xi + meta.x;
+        double *__restrict__ gv = P->v + meta.x;
+
+        for (int i = t; i < NB; i += NT)
+            s_hist[i] = 0u;
+        __syncthreads();
+
+        // sort keys of live SDs and their bucket slots
+        uint64_t key[2 * RP];
+        uint32_t slot[2 * RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+            const int q = t + r * NT;
+            slot[2 * r] = 0xFFFFFFFFu;
+            slot[2 * r + 1] = 0xFFFFFFFFu;
+            key[2 * r] = 0;
+            key[2 * r + 1] = 0;
+            if (2 * q < n) {
+                const bool la = xs[2 * q] > 0, lb = xs[2 * q + 1] > 0;
+                if (la | lb) {
+                    const uint4 w = draw4(seed, (uint32_t)q, cell, s, 0u);
+                    if (la) {
+                        key[2 * r] = ((uint64_t)w.x << 32) | w.y;
+                        slot[2 * r] = atomicAdd(&s_hist[key[2 * r] >> (64 - LB)], 1u);
+                    }
+                    if (lb) {
+                        key[2 * r + 1] = ((uint64_t)w.z << 32) | w.w;
+                        slot[2 * r + 1] = atomicAdd(&s_hist[key[2 * r + 1] >> (64 - LB)], 1u);
+                    }
+                }
             }
         }
+        __syncthreads();
+
+        // bucket starts; the total is the live count n_c
+        const uint32_t n_c = block_exclusive_scan<NT, NB>(s_hist, s_warp);
+        if (n_c >= 2) {
+            if (t == 0) {
+                const double sc = cell_scale(P->dtdv, (int64_t)n_c);
+                s_scale = sc;
+                s_scale_f = __double2float_rn(sc);
+            }
+            // scatter into bucket order
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (slot[2 * r + h] != 0xFFFFFFFFu) {
+                        const uint32_t pos = s_hist[key[2 * r + h] >> (64 - LB)] + slot[2 * r + h];
+                        s_key[pos] = key[2 * r + h];
+                        s_rank[pos] = (uint16_t)(2 * (t + r * NT) + h);
+                    }
+                }
+            }
+            __syncthreads();
+
+            // order within each bucket by (key, rank)
+            for (uint32_t pos = t; pos < n_c; pos += NT) {
+                const uint64_t kk = s_key[pos];
+                const uint32_t rk = s_rank[pos];
+                const uint32_t b = (uint32_t)(kk >> (64 - LB));
+                const uint32_t lo = s_hist[b];
+                const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
+                uint32_t cnt = 0;
+                for (uint32_t m = lo; m < hi; ++m)
+                    cnt += key_less(s_key[m], s_rank[m], kk, rk) ? 1u : 0u;
+                s_perm[lo + cnt] = (uint16_t)rk;
+            }
+            __syncthreads();
+
+            // pairs (l = 2q, 2q + 1 share one Philox block)
+            const uint32_t n_pairs = n_c / 2;
+            const double scale = s_scale;
+            const float scale_f = s_scale_f;
+            const PairConsts C = pair_consts(P);
+            for (uint32_t q = t; 2 * q < n_pairs; q += NT) {
+                const uint4 w = draw4(seed, q, cell, s, 1u);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t l = 2 * q + h;
+                    if (l >= n_pairs)
+                        break;
+                    int a = s_perm[2 * l], b = s_perm[2 * l + 1];
+                    int64_t xa = xs[a], xb = xs[b];
+                    if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
+                        const int tmp = a;
+                        a = b;
+                        b = tmp;
+                        const int64_t tx = xa;
+                        xa = xb;
+                        xb = tx;
+                    }
+                    double va = vs[a], vb = vs[b];
+                    const int64_t g = pair_gamma(P, C, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
+                    if (g > 0) {
+                        const bool split = shima_update(g, xa, xb, va, vb);
+                        gxi[a] = xa;
+                        gxi[b] = xb;
+                        gv[b] = vb;
+                        if (split)
+                            gv[a] = va;
+                    }
+                }
+            }
+        }
+        __syncthreads(); // stage sg and the work arrays are free again
     }
 }
 
@@ -290,7 +379,7 @@ __global__ void __launch_bounds__(kBigNT) big_hist_kernel(const BigChunk *__rest
                                                           const InstDev *const *__restrict__ insts,
                                                           BigScratch S, int64_t step_offset)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem_raw);
     const BigChunk ch = chunks[blockIdx.x];
     const BigCell bc = bigs[ch.big];
@@ -314,7 +403,7 @@ __global__ void __launch_bounds__(kBigNT) big_hist_kernel(const BigChunk *__rest
 __global__ void __launch_bounds__(kBigNT) big_scan_kernel(const BigCell *__restrict__ bigs,
                                                           const InstDev *const *__restrict__ insts, BigScratch S)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     uint32_t *s_tot = reinterpret_cast<uint32_t *>(smem_raw);
     __shared__ uint32_t s_warp[32];
     const BigCell bc = bigs[blockIdx.x];
@@ -349,7 +438,7 @@ __global__ void __launch_bounds__(kBigNT) big_scatter_kernel(const BigChunk *__r
                                                              const InstDev *const *__restrict__ insts,
                                                              BigScratch S, int64_t step_offset)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem_raw);
     const BigChunk ch = chunks[blockIdx.x];
     const BigCell bc = bigs[ch.big];
@@ -448,7 +537,7 @@ __global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBuc
 
 __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__restrict__ work,
                                                             const BigCell *__restrict__ bigs,
-                                                            const InstDev *const *__restrict__ insts,
+                                                            InstDev *const *__restrict__ insts,
                                                             BigScratch S, int64_t step_offset)
 {
     const BigPairs pw = work[blockIdx.x];
@@ -460,6 +549,7 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
     if (2 * q >= n_pairs)
         return;
     const InstDev *__restrict__ P = insts[bc.inst];
+    const PairConsts C = pair_consts(P);
     const int64_t s = P->step + step_offset;
     const int32_t off = P->cell_off[bc.cell];
     int64_t *__restrict__ gxi = P->xi + off;
@@ -484,7 +574,7 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
             xb = tx;
         }
         double va = gv[a], vb = gv[b];
-        const int64_t g = pair_gamma(*P, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
+        const int64_t g = pair_gamma(P, C, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
         if (g > 0) {
             const bool split = shima_update(g, xa, xb, va, vb);
             gxi[a] = xa;

@@ -189,25 +189,41 @@ int big_lb(int n)
 
 size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
 
-template <int CAP, int NT>
-cudaError_t configure_cell_kernel()
-{
-    return cudaFuncSetAttribute(cell_step_kernel<CAP, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)CellSmem<CAP>::bytes);
-}
+// Shared-memory classes: capacity, threads, pipeline stages.
+#define SDM_CELL_CLASSES(X)                                                                                            \
+    X(0, 64, 32, 4)                                                                                                    \
+    X(1, 128, 64, 4)                                                                                                   \
+    X(2, 256, 128, 4)                                                                                                  \
+    X(3, 512, 256, 4)                                                                                                  \
+    X(4, 1024, 512, 3)                                                                                                 \
+    X(5, 2048, 1024, 2)                                                                                                \
+    X(6, 4096, 1024, 2)
+
+int g_cell_grid[kNumClass]; // persistent CTAs per class (resident blocks x SMs)
 
 cudaError_t configure_kernels_once()
 {
     static cudaError_t status = [] {
-        cudaError_t e = cudaSuccess;
-        cudaError_t r;
-        if ((r = configure_cell_kernel<64, 32>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<128, 64>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<256, 128>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<512, 256>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<1024, 512>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<2048, 1024>()) != cudaSuccess) e = r;
-        if ((r = configure_cell_kernel<4096, 1024>()) != cudaSuccess) e = r;
+        cudaError_t e = cudaSuccess, r;
+        int dev = 0, sms = 0;
+        if ((r = cudaGetDevice(&dev)) != cudaSuccess)
+            return r;
+        if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return r;
+#define X(IDX, CAP, NT, ST)                                                                                            \
+    {                                                                                                                  \
+        const int bytes = (int)CellSmem<CAP, ST>::bytes;                                                               \
+        if ((r = cudaFuncSetAttribute(cell_step_kernel<CAP, NT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                      bytes)) != cudaSuccess)                                                          \
+            e = r;                                                                                                     \
+        int per_sm = 0;                                                                                                \
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_step_kernel<CAP, NT, ST>, NT, bytes)) != \
+            cudaSuccess)                                                                                               \
+            e = r;                                                                                                     \
+        g_cell_grid[IDX] = std::max(1, per_sm) * sms;                                                                  \
+    }
+        SDM_CELL_CLASSES(X)
+#undef X
         const int hb = (int)big_hist_smem(kBigMaxLB);
         if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
@@ -219,14 +235,14 @@ cudaError_t configure_kernels_once()
 
 void launch_cell_class(int cls, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
 {
+    const int grid = std::min(n, g_cell_grid[cls]);
     switch (cls) {
-    case 0: cell_step_kernel<64, 32><<<n, 32, CellSmem<64>::bytes, st>>>(items, insts, off); break;
-    case 1: cell_step_kernel<128, 64><<<n, 64, CellSmem<128>::bytes, st>>>(items, insts, off); break;
-    case 2: cell_step_kernel<256, 128><<<n, 128, CellSmem<256>::bytes, st>>>(items, insts, off); break;
-    case 3: cell_step_kernel<512, 256><<<n, 256, CellSmem<512>::bytes, st>>>(items, insts, off); break;
-    case 4: cell_step_kernel<1024, 512><<<n, 512, CellSmem<1024>::bytes, st>>>(items, insts, off); break;
-    case 5: cell_step_kernel<2048, 1024><<<n, 1024, CellSmem<2048>::bytes, st>>>(items, insts, off); break;
-    case 6: cell_step_kernel<4096, 1024><<<n, 1024, CellSmem<4096>::bytes, st>>>(items, insts, off); break;
+#define X(IDX, CAP, NT, ST)                                                                                            \
+    case IDX:                                                                                                          \
+        cell_step_kernel<CAP, NT, ST><<<grid, NT, CellSmem<CAP, ST>::bytes, st>>>(items, n, insts, off);               \
+        break;
+        SDM_CELL_CLASSES(X)
+#undef X
     }
 }
 
@@ -543,6 +559,18 @@ InstDev make_inst(const sdm_ctx *c)
     return d;
 }
 
+// Reads the run's device status word (after the stream has been synchronised).
+sdm_status check_device_status(sdm_ctx *ctx)
+{
+    uint32_t status = 0;
+    cudaError_t e = cudaMemcpy(&status, &ctx->d_inst->status, sizeof status, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "status read");
+    if (status & 1u)
+        return fail(&ctx->error, SDM_ETIMEOUT, "a device-side wait for a bulk copy gave up; results are incomplete");
+    return SDM_OK;
+}
+
 sdm_status ctx_usable(sdm_ctx *ctx)
 {
     if (!ctx)
@@ -813,6 +841,8 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     if (!out_on_device) {
         CTX_CUDA(ctx, cudaMemcpyAsync(out, d_out, b_acc, cudaMemcpyDeviceToHost, s));
         CTX_CUDA(ctx, cudaStreamSynchronize(s));
+        ctx->mem.put(tmp, b_tmp);
+        return check_device_status(ctx);
     }
     ctx->mem.put(tmp, b_tmp);
     return SDM_OK;
@@ -847,7 +877,7 @@ sdm_status sdm_get_attributes(sdm_ctx *ctx, int64_t *xi, double *volume, int on_
         CTX_CUDA(ctx, cudaMemcpyAsync(volume, tmp + bx, bv, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
     ctx->mem.put(tmp, bx + bv);
-    return SDM_OK;
+    return check_device_status(ctx);
 }
 
 sdm_status sdm_get_info(const sdm_ctx *ctx, sdm_info *out)
