@@ -193,6 +193,45 @@ sdm_status sdm_batch_destroy(sdm_batch *batch);
 
 const char *sdm_batch_last_error(const sdm_batch *batch);
 
+/* ---- allocation-free step of one cell.  This call has no counterpart in
+ * the paper; it exists for callers that cannot allocate device memory while
+ * they run: a host model that reserves all of its GPU memory up front in its
+ * own pool and forbids later allocation, a Fortran/OpenACC code whose runtime
+ * owns every device buffer, a latency-bound loop that cannot afford an
+ * allocator call.  It allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch is one fixed array of device
+ * memory inside the library (about 18 MiB for SDM_NOALLOC_MAX_SD SDs), which
+ * every GPU that loads the library holds until the process exits.
+ *
+ * One coalescence step (the same step as sdm_coalescence_step) of ONE cell
+ * whose SDs the caller holds, in place:
+ *   cfg       kernel, precision, golovin_b, dt, dv, Rogers-Yau coefficients
+ *             and seed as for sdm_create; n_cells must be 1; step0 and the
+ *             allocator hooks are ignored
+ *   step      index of this step (>= 0); the random streams use cell index 0
+ *   xi[n_sd]  int64 multiplicities, device memory, 16-byte aligned, SDs in
+ *             rank order (the order that addresses their random keys)
+ *   volume[n_sd]  binary64 volumes, device memory, 16-byte aligned
+ *   n_sd      even, in [2, SDM_NOALLOC_MAX_SD]; pad an odd cell with one dead
+ *             SD (xi = 0)
+ *   cuda_stream   stream the work is ordered on (NULL: legacy default stream)
+ * Values are not validated (they must satisfy sdm_set_attributes' ranges);
+ * sizes beyond the maximum are rejected with SDM_EINVAL.  The result equals
+ * sdm_coalescence_step on a context with one cell, the same config and
+ * step0 = step, bit for bit.  Returns after enqueueing the work.
+ *
+ * Set-up: the first call on each device (with that device current) looks up
+ * the scratch array's device address and configures the kernels; make that
+ * first call before any stream capture.  Every call shares the one array and
+ * leaves its contents behind, so calls whose work overlaps on the GPU (two
+ * streams, two host threads, two devices' calls aimed at one device) race:
+ * order them on one stream.  Errors: SDM_EINVAL, SDM_ECUDA (message from
+ * sdm_last_error(NULL)). */
+#define SDM_NOALLOC_MAX_SD 1048576
+
+sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step, int64_t *xi, double *volume, int64_t n_sd,
+                                 void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

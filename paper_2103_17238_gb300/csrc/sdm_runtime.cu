@@ -966,3 +966,6 @@ const char *sdm_batch_last_error(const sdm_batch *batch)
 }
 
 } // extern "C"
+
+// The allocation-free entry point, after the kernels and helpers it uses.
+#include "sdm_noalloc.cu"

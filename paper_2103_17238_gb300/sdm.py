@@ -29,7 +29,9 @@ EXPORTS = [
     "sdm_config_default", "sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
     "sdm_get_attributes", "sdm_get_info", "sdm_footprint_bytes", "sdm_destroy", "sdm_last_error",
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
+    "sdm_cell_step_noalloc",
 ]
+NOALLOC_MAX_SD = 1 << 20
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -109,9 +111,10 @@ def load(path: str = LIB_PATH):
         L.sdm_batch_destroy.argtypes = [vp]
         L.sdm_batch_last_error.argtypes = [vp]
         L.sdm_batch_last_error.restype = ctypes.c_char_p
+        L.sdm_cell_step_noalloc.argtypes = [P(sdm_config), i64, vp, vp, i64, vp]
         for name in ("sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
                      "sdm_get_attributes", "sdm_get_info", "sdm_destroy", "sdm_batch_create",
-                     "sdm_batch_step", "sdm_batch_destroy"):
+                     "sdm_batch_step", "sdm_batch_destroy", "sdm_cell_step_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -268,6 +271,19 @@ def sdm_batch_step(batch, n_steps: int = 1):
 def sdm_batch_destroy(batch):
     if batch:
         _check(load().sdm_batch_destroy(batch), "sdm_batch_destroy")
+
+
+def sdm_cell_step_noalloc(cfg: sdm_config, step: int, xi, volume, stream: int):
+    """One step of one cell held in caller device tensors (int64 xi, float64
+    volume), in place, without any device allocation by the library."""
+    px, dx, kx = _ptr_and_flag(xi, np.int64)
+    pv, dv_, kv = _ptr_and_flag(volume, np.float64)
+    if not (dx and dv_):
+        raise ValueError("xi and volume must be device tensors")
+    if kx.data_ptr() != xi.data_ptr() or kv.data_ptr() != volume.data_ptr():
+        raise ValueError("xi and volume must be contiguous (the step works in place)")
+    _check(load().sdm_cell_step_noalloc(ctypes.byref(cfg), int(step), px, pv, int(kx.shape[0]),
+                                        ctypes.c_void_p(stream)), "sdm_cell_step_noalloc")
 
 
 # ------------------------------------------------------------ owners
