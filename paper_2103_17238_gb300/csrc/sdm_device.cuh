@@ -31,6 +31,7 @@ struct InstDev {
     double b;                // Golovin constant
     double k1, k2, k3, r1, r2;
     float bf, k1f, k2f, k3f, r1f, r2f; // binary32 roundings of the above
+    float dtdvf;                       // dt / dv rounded to binary32 (filter only)
     int32_t kernel, precision, n_cells;
     uint32_t status; // bit 0: a bounded device wait gave up (reported as SDM_ETIMEOUT)
 };
@@ -43,6 +44,22 @@ struct WorkItem {
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // products with the Weyl key schedule.
+__device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t mullo32(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+// Separate high and low 32-bit products issue fewer instructions here than
+// one 64-bit product (measured on sm_103a).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 {
 #pragma unroll
@@ -51,10 +68,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
             k.x += 0x9E3779B9u;
             k.y += 0xBB67AE85u;
         }
-        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c.x;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k.y,
-                       (uint32_t)p0);
+        const uint32_t h0 = mulhi32(0xD2511F53u, c.x), l0 = mullo32(0xD2511F53u, c.x);
+        const uint32_t h1 = mulhi32(0xCD9E8D57u, c.z), l1 = mullo32(0xCD9E8D57u, c.z);
+        c = make_uint4(h1 ^ c.y ^ k.x, l1, h0 ^ c.w ^ k.y, l0);
     }
     return c;
 }
@@ -239,9 +255,19 @@ __device__ __forceinline__ int64_t gamma_exact(double p, double u, int64_t xi_j,
     return __double2ll_rz(g);
 }
 
+// dt/dV [n_c (n_c - 1) / 2] / floor(n_c / 2), once per cell.  The ratio is
+// exactly n_c - 1 for even n_c and n_c for odd n_c, so the IEEE quotient of
+// the definition equals that integer and no division is needed.
+__device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
+{
+    const int64_t ratio = (n_c & 1) ? n_c : n_c - 1;
+    return __dmul_rn(dtdv, __ll2double_rn(ratio));
+}
+
 // Per-run constants of the pair arithmetic, loaded once per cell.
 struct PairConsts {
     float bf, k1f, k2f, k3f, r1f, r2f;
+    float dtdvf; // dt / dV rounded to binary32 (filter only)
     int32_t kernel, precision;
 };
 
@@ -254,6 +280,7 @@ __device__ __forceinline__ PairConsts pair_consts(const InstDev *P)
     c.k3f = P->k3f;
     c.r1f = P->r1f;
     c.r2f = P->r2f;
+    c.dtdvf = P->dtdvf;
     c.kernel = P->kernel;
     c.precision = P->precision;
     return c;
@@ -268,59 +295,111 @@ __device__ __forceinline__ float vt32c(const PairConsts &C, float r)
     return __fmul_rn(C.k3f, __fsqrt_rn(r));
 }
 
-// The rare exact path: the binary64 definition (FP64 mode) or the widened
-// binary32 value (KFP32 mode), then gamma.
-__device__ __noinline__ int64_t gamma_slow(const InstDev *P, double scale, float pf, int64_t xi_j, int64_t xi_k,
-                                           double vj, double vk, uint32_t wa, uint32_t wb)
+// ------------------------------------------------------------- the filter
+// Filter-grade helpers: each has a stated relative error e, and the filter's
+// margin covers their sum with a wide factor.
+//   d2f_trunc      e < 2^-23 (truncation of the binary64 mantissa)
+//   cbrt_filter    e < 2^-18.9 (lg2/ex2 approximations; maximum 2^-18.99
+//                  measured exhaustively over every binary32 in
+//                  [2^-110, 2^110) on sm_103a against the binary64 cube root)
+__device__ __forceinline__ float d2f_trunc(double x, bool &in_range)
 {
-    const double p = P->precision == PREC_KFP32 ? (double)pf : probability_exact(*P, scale, xi_j, vj, vk);
-    return gamma_exact(p, uniform53(wa, wb), xi_j, xi_k);
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    in_range = (e - 897u) < 253u;
+    return __uint_as_float(((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
-// Collision count of one pair (xi_j >= xi_k > 0).  The binary32 stage is
-// itself the definition in KFP32 mode; in FP64 mode it is a filter: with
-// pf the binary32 value and M a binary32 magnitude of every term of p,
-// |pf - p| <= 2^-18.5 M (error analysis of the operations below, cube root
-// within 1 ulp), so pf + 2^-12 M + 2^-100 < u implies p < u, i.e. gamma = 0.
-// Near a terminal-velocity regime boundary, or when a binary32 value leaves
-// the normal range, the filter abstains and the exact path decides.
-__device__ __forceinline__ int64_t pair_gamma(const InstDev *P, const PairConsts &C, double scale, float scale_f,
-                                              int64_t xi_j, int64_t xi_k, double vj, double vk, uint32_t wa,
-                                              uint32_t wb)
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float cbrt_filter(float x) { return ex2_approx(lg2_approx(x) * 0x1.555556p-2f); }
+
+__device__ __forceinline__ float vt_filter(const PairConsts &C, float r)
+{
+    const float a = C.k1f * (r * r), b = C.k2f * r, c = C.k3f * sqrtf(r);
+    return r < C.r1f ? a : (r < C.r2f ? b : c);
+}
+
+// True when gamma = 0 is certain for the pair (xi_j >= xi_k > 0).  With pf
+// the filter's binary32 value of p and M a binary32 magnitude of all of p's
+// terms (K evaluated with |v_t(r_j) - v_t(r_k)| replaced by the sum), the
+// filter's error is below 2^-16.5 M (radius 2^-18.9, squares and fall speeds
+// 2^-17.8, the difference absolute in M) and the exact value's (binary64, or
+// binary32 with a 1-ulp cube root) below 2^-19 M, so pf + 2^-10 M + 2^-100 < u
+// implies p < u.  The filter abstains within 2^-14 of a terminal-velocity
+// regime boundary (radius error 2^-18.9) and when a binary32 value leaves
+// the normal range.
+__device__ __forceinline__ bool pair_certainly_zero(const PairConsts &C, float ratio_f, int64_t xi_j, double vj,
+                                                    double vk, uint32_t wa)
 {
     const float u_lo = uniform_lo23(wa);
     bool in_j, in_k;
-    const float vjf = d2f_rn(vj, in_j), vkf = d2f_rn(vk, in_k);
+    const float vjf = d2f_trunc(vj, in_j), vkf = d2f_trunc(vk, in_k);
     const float xjf = xi_to_f32_rn(xi_j);
+    const float sc = C.dtdvf * ratio_f;
     float pf, mag;
     bool ok = in_j & in_k;
     if (C.kernel == KERNEL_GOLOVIN) {
-        const float K = __fmul_rn(C.bf, __fadd_rn(vjf, vkf));
-        pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
+        const float K = C.bf * (vjf + vkf);
+        pf = (K * xjf) * sc;
         mag = pf;
         ok &= K >= 0x1p-126f;
     } else {
-        const float rj = radius32(vjf), rk = radius32(vkf);
-        const float tj = vt32c(C, rj), tk = vt32c(C, rk);
-        const float s = __fadd_rn(rj, rk);
-        const float a = __fmul_rn(kPiF, __fmul_rn(s, s));
-        const float K = __fmul_rn(a, fabsf(__fsub_rn(tj, tk)));
-        pf = __fmul_rn(__fmul_rn(K, xjf), scale_f);
+        const float rj = cbrt_filter(vjf * kVolToR3F), rk = cbrt_filter(vkf * kVolToR3F);
+        const float tj = vt_filter(C, rj), tk = vt_filter(C, rk);
+        const float s = rj + rk;
+        const float a = kPiF * (s * s);
+        const float K = a * fabsf(tj - tk);
+        pf = (K * xjf) * sc;
         const float km = a * (tj + tk);
-        mag = (km * xjf) * scale_f;
-        const float g1 = C.r1f * 0x1p-16f, g2 = C.r2f * 0x1p-16f;
+        mag = (km * xjf) * sc;
+        const float g1 = C.r1f * 0x1p-14f, g2 = C.r2f * 0x1p-14f;
         ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f) && fabsf(rj - C.r1f) > g1 &&
               fabsf(rk - C.r1f) > g1 && fabsf(rj - C.r2f) > g2 && fabsf(rk - C.r2f) > g2;
     }
-    if (C.precision == PREC_KFP32) {
-        if (ok && pf < u_lo)
-            return 0;
+    return ok && (pf + mag * 0x1p-10f + 0x1p-100f) < u_lo;
+}
+
+// ------------------------------------------------------------ exact gamma
+// The definition: p in binary64 (FP64 mode) or binary32 widened (KFP32
+// mode), then gamma.  Called for the pairs the filter could not decide,
+// compacted so that every lane of a warp has one.
+__device__ __forceinline__ int64_t pair_gamma_exact(const InstDev *P, uint32_t n_c, int64_t xi_j, int64_t xi_k,
+                                                    double vj, double vk, uint32_t wa, uint32_t wb)
+{
+    const double scale = cell_scale(P->dtdv, (int64_t)n_c);
+    double p;
+    if (P->precision == PREC_KFP32) {
+        const PairConsts C = pair_consts(P);
+        bool in_j, in_k;
+        const float vjf = d2f_rn(vj, in_j), vkf = d2f_rn(vk, in_k);
+        const float xjf = xi_to_f32_rn(xi_j);
+        const float scale_f = __double2float_rn(scale);
+        float K;
+        if (C.kernel == KERNEL_GOLOVIN) {
+            K = __fmul_rn(C.bf, __fadd_rn(vjf, vkf));
+        } else {
+            const float rj = radius32(vjf), rk = radius32(vkf);
+            const float s = __fadd_rn(rj, rk);
+            K = __fmul_rn(__fmul_rn(kPiF, __fmul_rn(s, s)), fabsf(__fsub_rn(vt32c(C, rj), vt32c(C, rk))));
+        }
+        p = (double)__fmul_rn(__fmul_rn(K, xjf), scale_f);
     } else {
-        const float p_hi = pf + mag * 0x1p-12f + 0x1p-100f;
-        if (ok && p_hi < u_lo)
-            return 0;
+        p = probability_exact(*P, scale, xi_j, vj, vk);
     }
-    return gamma_slow(P, scale, pf, xi_j, xi_k, vj, vk, wa, wb);
+    return gamma_exact(p, uniform53(wa, wb), xi_j, xi_k);
 }
 
 // Shima update for gamma > 0.  Returns true when the j SD's volume changed
@@ -342,13 +421,5 @@ __device__ __forceinline__ bool shima_update(int64_t gamma, int64_t &xi_j, int64
     return true;
 }
 
-// dt/dV [n_c (n_c - 1) / 2] / floor(n_c / 2), once per cell.  The ratio is
-// exactly n_c - 1 for even n_c and n_c for odd n_c, so the IEEE quotient of
-// the definition equals that integer and no division is needed.
-__device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
-{
-    const int64_t ratio = (n_c & 1) ? n_c : n_c - 1;
-    return __dmul_rn(dtdv, __ll2double_rn(ratio));
-}
 
 } // namespace sdm

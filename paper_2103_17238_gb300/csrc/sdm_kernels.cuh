@@ -123,15 +123,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 }
 
 // -------------------------------------------------------------- cell step
+// A pair the filter could not decide, waiting for the exact evaluation.
+struct QEntry {
+    int64_t xj, xk;
+    double vj, vk;
+    uint32_t slot_j, slot_k; // storage slots in the run's arrays
+    uint32_t wa, wb;         // the pair's uniform words
+    uint32_t n_c;            // live SDs of its cell
+    int32_t inst;            // its run
+};
+
+constexpr int kQueueFlush = 64; // flush once this many pairs wait
+
+template <int CAP>
+struct QueueCap {
+    static constexpr int value = (kQueueFlush + CAP / 2) < 512 ? (kQueueFlush + CAP / 2) : 512;
+};
+
 template <int CAP, int STAGES>
 struct CellSmem {
-    // STAGES x (xi, v) staging + key, bucket, rank, perm work arrays
-    static constexpr size_t bytes = (size_t)CAP * (16 * STAGES + 8 + 4 + 2 + 2);
+    // STAGES x (xi, v) staging + key, bucket, rank, perm work arrays + queue
+    static constexpr size_t bytes =
+        (size_t)CAP * (16 * STAGES + 8 + 4 + 2 + 2) + sizeof(QEntry) * (size_t)QueueCap<CAP>::value;
 };
 
 // Persistent: CTA b handles work items b, b + gridDim.x, ...  Thread 0
 // streams the next STAGES - 1 cells into shared memory with bulk copies
-// while the CTA works on the current one.
+// while the CTA works on the current one.  Pairs the binary32 filter cannot
+// decide wait in a shared-memory queue (across cells) and are evaluated
+// exactly, one per lane, when kQueueFlush of them have gathered and at the
+// end: every SD belongs to one pair per step and nothing reads it again in
+// this launch, so deferring its update is safe.
 template <int CAP, int NT, int STAGES>
 __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
                                                        InstDev *const *__restrict__ insts, int64_t step_offset)
@@ -149,19 +171,42 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_key + CAP);
     uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + NB);
     uint16_t *s_perm = s_rank + CAP;
+    QEntry *s_q = reinterpret_cast<QEntry *>(s_perm + CAP);
+    constexpr uint32_t QCAP = QueueCap<CAP>::value;
+    __shared__ uint32_t s_qn;
     __shared__ uint64_t s_bar[STAGES];
     __shared__ int4 s_meta[STAGES]; // off, n, cell, inst
     __shared__ uint32_t s_warp[32];
-    __shared__ double s_scale;
-    __shared__ float s_scale_f;
 
     const int t = threadIdx.x;
     if (t == 0) {
         for (int i = 0; i < STAGES; ++i)
             mbar_init(&s_bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_qn = 0;
     }
     __syncthreads();
+
+    auto flush = [&]() { // all threads; the queue's contents are visible to all
+        const uint32_t nq = s_qn < QCAP ? s_qn : QCAP;
+        for (uint32_t e = t; e < nq; e += NT) {
+            QEntry E = s_q[e];
+            InstDev *Pq = insts[E.inst];
+            const int64_t g = pair_gamma_exact(Pq, E.n_c, E.xj, E.xk, E.vj, E.vk, E.wa, E.wb);
+            if (g > 0) {
+                const bool split = shima_update(g, E.xj, E.xk, E.vj, E.vk);
+                Pq->xi[E.slot_j] = E.xj;
+                Pq->xi[E.slot_k] = E.xk;
+                Pq->v[E.slot_k] = E.vk;
+                if (split)
+                    Pq->v[E.slot_j] = E.vj;
+            }
+        }
+        __syncthreads();
+        if (t == 0)
+            s_qn = 0;
+        __syncthreads();
+    };
 
     auto issue = [&](int k) { // thread 0: start loading the k-th cell of this CTA
         const int i = blockIdx.x + k * gridDim.x;
@@ -243,11 +288,6 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
         // bucket starts; the total is the live count n_c
         const uint32_t n_c = block_exclusive_scan<NT, NB>(s_hist, s_warp);
         if (n_c >= 2) {
-            if (t == 0) {
-                const double sc = cell_scale(P->dtdv, (int64_t)n_c);
-                s_scale = sc;
-                s_scale_f = __double2float_rn(sc);
-            }
             // scatter into bucket order
 #pragma unroll
             for (int r = 0; r < RP; ++r) {
@@ -276,10 +316,10 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
             }
             __syncthreads();
 
-            // pairs (l = 2q, 2q + 1 share one Philox block)
+            // pairs (l = 2q, 2q + 1 share one Philox block): the filter
+            // settles almost all; the rest join the queue
             const uint32_t n_pairs = n_c / 2;
-            const double scale = s_scale;
-            const float scale_f = s_scale_f;
+            const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
             const PairConsts C = pair_consts(P);
             for (uint32_t q = t; 2 * q < n_pairs; q += NT) {
                 const uint4 w = draw4(seed, q, cell, s, 1u);
@@ -299,20 +339,330 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
                         xb = tx;
                     }
                     double va = vs[a], vb = vs[b];
-                    const int64_t g = pair_gamma(P, C, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
-                    if (g > 0) {
-                        const bool split = shima_update(g, xa, xb, va, vb);
-                        gxi[a] = xa;
-                        gxi[b] = xb;
-                        gv[b] = vb;
-                        if (split)
-                            gv[a] = va;
+                    const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
+                    if (pair_certainly_zero(C, ratio_f, xa, va, vb, wa))
+                        continue;
+                    const uint32_t qi = atomicAdd(&s_qn, 1u);
+                    if (qi < QCAP) {
+                        QEntry E;
+                        E.xj = xa;
+                        E.xk = xb;
+                        E.vj = va;
+                        E.vk = vb;
+                        E.slot_j = (uint32_t)(meta.x + a);
+                        E.slot_k = (uint32_t)(meta.x + b);
+                        E.wa = wa;
+                        E.wb = wb;
+                        E.n_c = n_c;
+                        E.inst = meta.w;
+                        s_q[qi] = E;
+                    } else { // queue full: evaluate here
+                        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                        if (g > 0) {
+                            const bool split = shima_update(g, xa, xb, va, vb);
+                            gxi[a] = xa;
+                            gxi[b] = xb;
+                            gv[b] = vb;
+                            if (split)
+                                gv[a] = va;
+                        }
                     }
                 }
             }
         }
         __syncthreads(); // stage sg and the work arrays are free again
+        if (s_qn >= (uint32_t)kQueueFlush)
+            flush();
     }
+    if (s_qn > 0)
+        flush();
+}
+
+// ------------------------------------------------------ warp-per-cell step
+// Cells of at most 256 stored SDs: one warp per cell, no block barriers.
+// Each warp runs its own bulk-copy pipeline (STAGES deep, one mbarrier per
+// stage), sorts its cell with the same one-pass bucket sort (a warp scan of
+// the bucket counts), and keeps its own queue of undecided pairs, which it
+// evaluates exactly, one pair per lane, once 32 have gathered.  Queue entries
+// hold storage slots only: the flush re-reads xi and v of its pairs from
+// global memory (this launch changes an SD only when its own pair is done).
+struct WQEntry {
+    uint32_t slot_j, slot_k; // storage slots in the run's arrays
+    uint32_t wa, wb;         // the pair's uniform words
+    uint32_t n_c;            // live SDs of its cell
+    int32_t inst;            // its run
+};
+
+constexpr int kWarpQueue = 96;
+
+template <int CAP, int STAGES>
+struct WarpSmem {
+    // per warp: STAGES x (xi, v), key, bucket, rank, perm, queue
+    static constexpr size_t per_warp =
+        (size_t)CAP * (16 * STAGES + 8 + 4 + 2 + 2) + sizeof(WQEntry) * (size_t)kWarpQueue;
+};
+
+template <int CAP, int WARPS, int STAGES>
+__global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
+                                                                    InstDev *const *__restrict__ insts,
+                                                                    int64_t step_offset)
+{
+    constexpr int NB = CAP;
+    constexpr int LB = ilog2_c(CAP);
+    constexpr int RP = CAP / 64 > 0 ? CAP / 64 : 1; // rank pairs per lane
+    constexpr int BPL = NB / 32;                   // buckets per lane in the scan
+    static_assert((1 << LB) == CAP && CAP >= 64 && CAP <= 256, "warp kernel: CAP in 64..256");
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *mine = smem_raw + (size_t)warp * WarpSmem<CAP, STAGES>::per_warp;
+    int64_t *st_xi = reinterpret_cast<int64_t *>(mine);               // [STAGES][CAP]
+    double *st_v = reinterpret_cast<double *>(st_xi + STAGES * CAP);  // [STAGES][CAP]
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(st_v + STAGES * CAP);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_key + CAP);
+    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + NB);
+    uint16_t *s_perm = s_rank + CAP;
+    WQEntry *s_q = reinterpret_cast<WQEntry *>(s_perm + CAP);
+    __shared__ uint64_t s_bar_all[WARPS][STAGES];
+    __shared__ int4 s_meta_all[WARPS][STAGES];
+    __shared__ uint32_t s_qn_all[WARPS];
+    uint64_t *s_bar = s_bar_all[warp];
+    int4 *s_meta = s_meta_all[warp];
+    uint32_t &s_qn = s_qn_all[warp];
+
+    const int gw = blockIdx.x * WARPS + warp;
+    const int nw = gridDim.x * WARPS;
+    if (lane == 0) {
+        for (int i = 0; i < STAGES; ++i)
+            mbar_init(&s_bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_qn = 0;
+    }
+    __syncwarp();
+
+    auto issue = [&](int k) { // lane 0: start loading this warp's k-th cell
+        const int i = gw + k * nw;
+        if (i >= n_items)
+            return;
+        const int sg = k % STAGES;
+        const WorkItem it = items[i];
+        const InstDev *P = insts[it.inst];
+        const int32_t off = P->cell_off[it.cell];
+        const int32_t n = P->cell_off[it.cell + 1] - off;
+        s_meta[sg] = make_int4(off, n, it.cell, it.inst);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)n * 16u);
+        bulk_g2s(st_xi + sg * CAP, P->xi + off, (uint32_t)n * 8u, &s_bar[sg]);
+        bulk_g2s(st_v + sg * CAP, P->v + off, (uint32_t)n * 8u, &s_bar[sg]);
+    };
+
+    auto flush = [&]() { // whole warp
+        const uint32_t nq = s_qn < (uint32_t)kWarpQueue ? s_qn : (uint32_t)kWarpQueue;
+        for (uint32_t e = lane; e < nq; e += 32) {
+            const WQEntry E = s_q[e];
+            InstDev *Pq = insts[E.inst];
+            int64_t xj = Pq->xi[E.slot_j], xk = Pq->xi[E.slot_k];
+            double vj = Pq->v[E.slot_j], vk = Pq->v[E.slot_k];
+            const int64_t g = pair_gamma_exact(Pq, E.n_c, xj, xk, vj, vk, E.wa, E.wb);
+            if (g > 0) {
+                const bool split = shima_update(g, xj, xk, vj, vk);
+                Pq->xi[E.slot_j] = xj;
+                Pq->xi[E.slot_k] = xk;
+                Pq->v[E.slot_k] = vk;
+                if (split)
+                    Pq->v[E.slot_j] = vj;
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            s_qn = 0;
+        __syncwarp();
+    };
+
+    if (lane == 0)
+        for (int k = 0; k < STAGES - 1; ++k)
+            issue(k);
+
+    for (int k = 0; gw + k * nw < n_items; ++k) {
+        if (lane == 0)
+            issue(k + STAGES - 1);
+        const int sg = k % STAGES;
+        const bool arrived = mbar_wait_bounded(&s_bar[sg], (uint32_t)(k / STAGES) & 1u);
+        if (!__all_sync(FULL, arrived)) {
+            if (lane == 0) {
+                atomicOr(&insts[s_meta[sg].w]->status, 1u);
+                for (int kk = k; kk < k + STAGES; ++kk)
+                    if (gw + kk * nw < n_items)
+                        mbar_wait_bounded(&s_bar[kk % STAGES], (uint32_t)(kk / STAGES) & 1u);
+            }
+            return;
+        }
+        const int4 meta = s_meta[sg];
+        const int n = meta.y;
+        const uint32_t cell = (uint32_t)meta.z;
+        InstDev *__restrict__ P = insts[meta.w];
+        const int64_t s = P->step + step_offset;
+        const uint64_t seed = P->seed;
+        const int64_t *xs = st_xi + sg * CAP;
+        const double *vs = st_v + sg * CAP;
+        int64_t *__restrict__ gxi = P->xi + meta.x;
+        double *__restrict__ gv = P->v + meta.x;
+
+#pragma unroll
+        for (int i = 0; i < BPL; ++i)
+            s_hist[lane + 32 * i] = 0u;
+        __syncwarp();
+
+        // sort keys of live SDs and their bucket slots
+        uint64_t key[2 * RP];
+        uint32_t slot[2 * RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+            const int q = lane + 32 * r;
+            slot[2 * r] = 0xFFFFFFFFu;
+            slot[2 * r + 1] = 0xFFFFFFFFu;
+            key[2 * r] = 0;
+            key[2 * r + 1] = 0;
+            if (2 * q < n) {
+                const bool la = xs[2 * q] > 0, lb = xs[2 * q + 1] > 0;
+                if (la | lb) {
+                    const uint4 w = draw4(seed, (uint32_t)q, cell, s, 0u);
+                    if (la) {
+                        key[2 * r] = ((uint64_t)w.x << 32) | w.y;
+                        slot[2 * r] = atomicAdd(&s_hist[key[2 * r] >> (64 - LB)], 1u);
+                    }
+                    if (lb) {
+                        key[2 * r + 1] = ((uint64_t)w.z << 32) | w.w;
+                        slot[2 * r + 1] = atomicAdd(&s_hist[key[2 * r + 1] >> (64 - LB)], 1u);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+
+        // bucket starts by a warp scan; the total is n_c
+        uint32_t cnt[BPL], sum = 0;
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) {
+            cnt[i] = s_hist[lane * BPL + i];
+            sum += cnt[i];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        const uint32_t n_c = __shfl_sync(FULL, incl, 31);
+        uint32_t run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) {
+            s_hist[lane * BPL + i] = run;
+            run += cnt[i];
+        }
+        __syncwarp();
+
+        if (n_c >= 2) {
+#pragma unroll
+            for (int r = 0; r < RP; ++r) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (slot[2 * r + h] != 0xFFFFFFFFu) {
+                        const uint32_t pos = s_hist[key[2 * r + h] >> (64 - LB)] + slot[2 * r + h];
+                        s_key[pos] = key[2 * r + h];
+                        s_rank[pos] = (uint16_t)(2 * (lane + 32 * r) + h);
+                    }
+                }
+            }
+            __syncwarp();
+            for (uint32_t pos = lane; pos < n_c; pos += 32) {
+                const uint64_t kk = s_key[pos];
+                const uint32_t rk = s_rank[pos];
+                const uint32_t b = (uint32_t)(kk >> (64 - LB));
+                const uint32_t lo = s_hist[b];
+                const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
+                uint32_t c = 0;
+                for (uint32_t m = lo; m < hi; ++m)
+                    c += key_less(s_key[m], s_rank[m], kk, rk) ? 1u : 0u;
+                s_perm[lo + c] = (uint16_t)rk;
+            }
+            __syncwarp();
+
+            const uint32_t n_pairs = n_c / 2;
+            const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
+            const PairConsts C = pair_consts(P);
+            const uint32_t n_q = (n_pairs + 1) / 2;
+            for (uint32_t q0 = 0; q0 < n_q; q0 += 32) { // warp-uniform trip count
+                const uint32_t q = q0 + lane;
+                const uint4 w = draw4(seed, q, cell, s, 1u);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t l = 2 * q + h;
+                    const bool valid = q < n_q && l < n_pairs;
+                    int a = 0, b = 0;
+                    int64_t xa = 0, xb = 0;
+                    double va = 0.0, vb = 0.0;
+                    bool und = false;
+                    const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
+                    if (valid) {
+                        a = s_perm[2 * l];
+                        b = s_perm[2 * l + 1];
+                        xa = xs[a];
+                        xb = xs[b];
+                        if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
+                            const int tmp = a;
+                            a = b;
+                            b = tmp;
+                            const int64_t tx = xa;
+                            xa = xb;
+                            xb = tx;
+                        }
+                        va = vs[a];
+                        vb = vs[b];
+                        und = !pair_certainly_zero(C, ratio_f, xa, va, vb, wa);
+                    }
+                    const unsigned m = __ballot_sync(FULL, und);
+                    if (m) {
+                        const uint32_t base = s_qn;
+                        const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
+                        if (und) {
+                            if (idx < (uint32_t)kWarpQueue) {
+                                WQEntry E;
+                                E.slot_j = (uint32_t)(meta.x + a);
+                                E.slot_k = (uint32_t)(meta.x + b);
+                                E.wa = wa;
+                                E.wb = wb;
+                                E.n_c = n_c;
+                                E.inst = meta.w;
+                                s_q[idx] = E;
+                            } else { // queue full: evaluate here
+                                const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                                if (g > 0) {
+                                    const bool split = shima_update(g, xa, xb, va, vb);
+                                    gxi[a] = xa;
+                                    gxi[b] = xb;
+                                    gv[b] = vb;
+                                    if (split)
+                                        gv[a] = va;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0)
+                            s_qn = base + (uint32_t)__popc(m);
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+        __syncwarp(); // stage sg and the work arrays are free again
+        if (s_qn >= 32u)
+            flush();
+    }
+    if (s_qn > 0)
+        flush();
 }
 
 // ----------------------------------------------------------- big cells
@@ -555,8 +905,7 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
     int64_t *__restrict__ gxi = P->xi + off;
     double *__restrict__ gv = P->v + off;
     const uint32_t *perm = S.perm + bc.sd_base;
-    const double scale = S.scale[big];
-    const float scale_f = S.scale_f[big];
+    const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
     const uint4 w = draw4(P->seed, q, (uint32_t)bc.cell, s, 1u);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -574,7 +923,10 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
             xb = tx;
         }
         double va = gv[a], vb = gv[b];
-        const int64_t g = pair_gamma(P, C, scale, scale_f, xa, xb, va, vb, h ? w.z : w.x, h ? w.w : w.y);
+        const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
+        if (pair_certainly_zero(C, ratio_f, xa, va, vb, wa))
+            continue;
+        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
         if (g > 0) {
             const bool split = shima_update(g, xa, xb, va, vb);
             gxi[a] = xa;

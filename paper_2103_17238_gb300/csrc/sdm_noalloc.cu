@@ -153,6 +153,7 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     inst.k3f = (float)inst.k3;
     inst.r1f = (float)inst.r1;
     inst.r2f = (float)inst.r2;
+    inst.dtdvf = (float)inst.dtdv;
     inst.kernel = cfg->kernel;
     inst.precision = cfg->precision;
     inst.n_cells = 1;

@@ -189,17 +189,20 @@ int big_lb(int n)
 
 size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
 
-// Shared-memory classes: capacity, threads, pipeline stages.
+// Shared-memory classes.  Up to 256 SDs: one warp per cell (capacity,
+// warps per block, pipeline stages); larger: one block per cell (capacity,
+// threads, stages).
+#define SDM_WARP_CLASSES(X)                                                                                            \
+    X(0, 64, 4, 2)                                                                                                     \
+    X(1, 128, 4, 2)                                                                                                    \
+    X(2, 256, 2, 2)
 #define SDM_CELL_CLASSES(X)                                                                                            \
-    X(0, 64, 32, 4)                                                                                                    \
-    X(1, 128, 64, 4)                                                                                                   \
-    X(2, 256, 128, 4)                                                                                                  \
     X(3, 512, 256, 4)                                                                                                  \
     X(4, 1024, 512, 3)                                                                                                 \
     X(5, 2048, 1024, 2)                                                                                                \
     X(6, 4096, 1024, 2)
 
-int g_cell_grid[kNumClass]; // persistent CTAs per class (resident blocks x SMs)
+int g_cell_grid[kNumClass]; // persistent blocks per class (resident blocks x SMs)
 
 cudaError_t configure_kernels_once()
 {
@@ -210,6 +213,20 @@ cudaError_t configure_kernels_once()
             return r;
         if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return r;
+#define X(IDX, CAP, WARPS, ST)                                                                                         \
+    {                                                                                                                  \
+        const int bytes = (int)(WarpSmem<CAP, ST>::per_warp * WARPS);                                                  \
+        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, WARPS, ST>,                                           \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)             \
+            e = r;                                                                                                     \
+        int per_sm = 0;                                                                                                \
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, WARPS, ST>,         \
+                                                               32 * WARPS, bytes)) != cudaSuccess)                     \
+            e = r;                                                                                                     \
+        g_cell_grid[IDX] = std::max(1, per_sm) * sms;                                                                  \
+    }
+        SDM_WARP_CLASSES(X)
+#undef X
 #define X(IDX, CAP, NT, ST)                                                                                            \
     {                                                                                                                  \
         const int bytes = (int)CellSmem<CAP, ST>::bytes;                                                               \
@@ -235,12 +252,22 @@ cudaError_t configure_kernels_once()
 
 void launch_cell_class(int cls, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
 {
-    const int grid = std::min(n, g_cell_grid[cls]);
     switch (cls) {
+#define X(IDX, CAP, WARPS, ST)                                                                                         \
+    case IDX: {                                                                                                        \
+        const int grid = std::min((n + WARPS - 1) / WARPS, g_cell_grid[IDX]);                                          \
+        warp_cell_step_kernel<CAP, WARPS, ST>                                                                          \
+            <<<grid, 32 * WARPS, WarpSmem<CAP, ST>::per_warp * WARPS, st>>>(items, n, insts, off);                     \
+        break;                                                                                                         \
+    }
+        SDM_WARP_CLASSES(X)
+#undef X
 #define X(IDX, CAP, NT, ST)                                                                                            \
-    case IDX:                                                                                                          \
+    case IDX: {                                                                                                        \
+        const int grid = std::min(n, g_cell_grid[IDX]);                                                                \
         cell_step_kernel<CAP, NT, ST><<<grid, NT, CellSmem<CAP, ST>::bytes, st>>>(items, n, insts, off);               \
-        break;
+        break;                                                                                                         \
+    }
         SDM_CELL_CLASSES(X)
 #undef X
     }
@@ -553,6 +580,7 @@ InstDev make_inst(const sdm_ctx *c)
     d.k3f = (float)d.k3;
     d.r1f = (float)d.r1;
     d.r2f = (float)d.r2;
+    d.dtdvf = (float)d.dtdv;
     d.kernel = c->cfg.kernel;
     d.precision = c->cfg.precision;
     d.n_cells = c->cfg.n_cells;

@@ -1,0 +1,155 @@
+"""Continuous-batching server of coalescence runs on one GPU.
+
+Requests (a Golovin box or a geometric cell grid, each with its own size,
+length, dt, spectrum and seed) arrive over time.  Admission is by device
+memory: a request enters as soon as it has arrived and its footprint
+(``sdm_footprint_bytes``) fits in what the budget has left.  Admitted runs
+keep their state resident and advance together: at every tick the active set
+is stepped by one fused batch (``sdm_batch_step``) of ``chunk`` steps, capped
+so that no run overshoots its own length.  Runs that finish hand back their
+dv/dlnr spectrum and final state and leave; their memory admits the next
+ones.  Every run keeps its own seed and step counter, so its result is the
+same alone and in any mix.
+
+Metrics: per-run step latency (tick wall time / steps of the tick, each run
+in the tick), time in system, and aggregate pair-updates/s.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs as I
+from . import sdm
+
+
+@dataclass
+class Served:
+    req: I.Request
+    run: sdm.Run | None = None
+    done: int = 0
+    admitted_at: float | None = None
+    finished_at: float | None = None
+    step_latency_ms: list = field(default_factory=list)
+    spectrum: np.ndarray | None = None
+    xi: np.ndarray | None = None
+    v: np.ndarray | None = None
+    footprint: int = 0
+    pairs_per_step: int = 0
+
+
+def footprint(inst: I.Instance) -> int:
+    largest = int(np.bincount(inst.cell, minlength=inst.n_cells).max())
+    return sdm.sdm_footprint_bytes(inst.n_sd, inst.n_cells, largest)
+
+
+def make_run(inst: I.Instance) -> sdm.Run:
+    cfg = sdm.make_config(inst.kernel, "fp64", b=inst.b, dt=inst.dt, dv=inst.dv, n_cells=inst.n_cells,
+                          seed=inst.seed)
+    return sdm.Run(cfg, inst.n_sd).set_attributes(inst.xi, inst.v, inst.cell)
+
+
+class Server:
+    def __init__(self, budget_bytes: int, chunk: int = 20, keep_state: bool = False, use_graph: bool = False,
+                 time_scale: float = 1.0):
+        self.budget = int(budget_bytes)
+        self.chunk = int(chunk)
+        self.keep_state = keep_state
+        self.use_graph = use_graph
+        self.time_scale = time_scale  # arrival times are divided by this
+
+    def serve(self, requests: list[I.Request]) -> dict:
+        import torch
+
+        pending = [Served(r) for r in sorted(requests, key=lambda r: r.arrival)]
+        for s in pending:
+            s.footprint = footprint(s.req.inst)
+            if s.footprint > self.budget:
+                raise sdm.SdmError(sdm.SDM_EBUDGET, "serve", f"request needs {s.footprint} B > budget")
+            live = np.bincount(s.req.inst.cell[s.req.inst.xi > 0], minlength=s.req.inst.n_cells)
+            s.pairs_per_step = int((live // 2).sum())
+        active: list[Served] = []
+        finished: list[Served] = []
+        used = 0
+        batch = None
+        members = None
+        ticks = 0
+        max_active = 0
+        max_used = 0
+        t0 = time.perf_counter()
+        pair_updates = 0
+        while pending or active:
+            now = (time.perf_counter() - t0) * self.time_scale
+            # admit every arrived request that fits (arrival order)
+            admitted = False
+            while pending and pending[0].req.arrival <= now and used + pending[0].footprint <= self.budget:
+                s = pending.pop(0)
+                s.run = make_run(s.req.inst)
+                s.admitted_at = time.perf_counter() - t0
+                used += s.footprint
+                active.append(s)
+                admitted = True
+            if not active:
+                # idle until the next arrival
+                wait = pending[0].req.arrival / self.time_scale - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+                continue
+            if admitted or batch is None or members != [id(s) for s in active]:
+                if batch is not None:
+                    batch.close()
+                batch = sdm.Batch([s.run for s in active], use_graph=self.use_graph, graph_steps=self.chunk)
+                members = [id(s) for s in active]
+            max_active = max(max_active, len(active))
+            max_used = max(max_used, used)
+            k = min(self.chunk, min(s.req.inst.steps - s.done for s in active))
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            batch.step(k)
+            torch.cuda.synchronize()
+            dt_ms = (time.perf_counter() - ts) * 1e3
+            ticks += 1
+            for s in active:
+                s.done += k
+                s.step_latency_ms.append(dt_ms / k)
+                pair_updates += k * s.pairs_per_step
+            still = []
+            for s in active:
+                if s.done >= s.req.inst.steps:
+                    s.spectrum = s.run.spectrum(I.R_EDGES)
+                    if self.keep_state:
+                        s.xi, s.v = s.run.attributes()
+                    s.finished_at = time.perf_counter() - t0
+                    used -= s.footprint
+                    finished.append(s)
+                else:
+                    still.append(s)
+            if len(still) != len(active):
+                batch.close()
+                batch = None
+                for s in active:
+                    if s not in still:
+                        s.run.close()
+                        s.run = None
+                active = still
+        if batch is not None:
+            batch.close()
+        wall = time.perf_counter() - t0
+        lat = np.concatenate([np.asarray(s.step_latency_ms) for s in finished]) if finished else np.zeros(0)
+        tis = np.array([s.finished_at - s.req.arrival / self.time_scale for s in finished])
+        return {
+            "served": finished,
+            "requests": len(finished),
+            "ticks": ticks,
+            "max_active": max_active,
+            "max_used_bytes": max_used,
+            "wall_s": wall,
+            "pair_updates": pair_updates,
+            "pair_updates_per_s": pair_updates / wall if wall > 0 else 0.0,
+            "step_latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
+                                "p99": float(np.percentile(lat, 99)) if lat.size else None},
+            "time_in_system_s": {"p50": float(np.percentile(tis, 50)) if tis.size else None,
+                                 "p99": float(np.percentile(tis, 99)) if tis.size else None},
+        }
