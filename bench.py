@@ -46,7 +46,7 @@ UNIT = "pair-updates/s"
 RUN_STEPS = 600
 WORKLOAD = ("grid_geometric: 128x128 cells x 256 SDs (4,194,304 SDs), dV=1e3 m^3, lognormal r_g=15um "
             "sigma_g=1.4 1e8 m^-3, geometric kernel (Rogers-Yau), dt=1 s, 600-step runs, FP64 p, int64 xi")
-KERNEL_NAME = "cell_step_kernel<256,128>"
+KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
 

@@ -267,7 +267,8 @@ __device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
 // Per-run constants of the pair arithmetic, loaded once per cell.
 struct PairConsts {
     float bf, k1f, k2f, k3f, r1f, r2f;
-    float dtdvf; // dt / dV rounded to binary32 (filter only)
+    float dtdvf;                  // dt / dV rounded to binary32 (filter only)
+    float r1_lo, r1_hi, r2_lo, r2_hi; // regime bounds widened by 2^-14 (filter only)
     int32_t kernel, precision;
 };
 
@@ -281,6 +282,10 @@ __device__ __forceinline__ PairConsts pair_consts(const InstDev *P)
     c.r1f = P->r1f;
     c.r2f = P->r2f;
     c.dtdvf = P->dtdvf;
+    c.r1_lo = c.r1f * (1.0f - 0x1p-14f);
+    c.r1_hi = c.r1f * (1.0f + 0x1p-14f);
+    c.r2_lo = c.r2f * (1.0f - 0x1p-14f);
+    c.r2_hi = c.r2f * (1.0f + 0x1p-14f);
     c.kernel = P->kernel;
     c.precision = P->precision;
     return c;
@@ -298,17 +303,11 @@ __device__ __forceinline__ float vt32c(const PairConsts &C, float r)
 // ------------------------------------------------------------- the filter
 // Filter-grade helpers: each has a stated relative error e, and the filter's
 // margin covers their sum with a wide factor.
-//   d2f_trunc      e < 2^-23 (truncation of the binary64 mantissa)
+//   hi2f           e < 2^-20 (the binary64's top 20 mantissa bits)
+//   xi2f           e < 2^-23 (truncating conversion)
 //   cbrt_filter    e < 2^-18.9 (lg2/ex2 approximations; maximum 2^-18.99
 //                  measured exhaustively over every binary32 in
 //                  [2^-110, 2^110) on sm_103a against the binary64 cube root)
-__device__ __forceinline__ float d2f_trunc(double x, bool &in_range)
-{
-    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-    const uint32_t e = (hi >> 20) & 0x7FFu;
-    in_range = (e - 897u) < 253u;
-    return __uint_as_float(((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-}
 
 __device__ __forceinline__ float lg2_approx(float x)
 {
@@ -326,31 +325,60 @@ __device__ __forceinline__ float ex2_approx(float x)
 
 __device__ __forceinline__ float cbrt_filter(float x) { return ex2_approx(lg2_approx(x) * 0x1.555556p-2f); }
 
-__device__ __forceinline__ float vt_filter(const PairConsts &C, float r)
+
+// Binary32 image of a positive binary64 from its high word alone: the top
+// 20 mantissa bits (relative error < 2^-20), exponent rebiased.  in_range:
+// the result is a normal binary32 (exponent field 1..253).
+__device__ __forceinline__ float hi2f(uint32_t hi, bool &in_range)
 {
-    const float a = C.k1f * (r * r), b = C.k2f * r, c = C.k3f * sqrtf(r);
-    return r < C.r1f ? a : (r < C.r2f ? b : c);
+    in_range = (hi - (897u << 20)) < (253u << 20);
+    return __uint_as_float((hi << 3) - (896u << 23));
 }
 
-// True when gamma = 0 is certain for the pair (xi_j >= xi_k > 0).  With pf
-// the filter's binary32 value of p and M a binary32 magnitude of all of p's
-// terms (K evaluated with |v_t(r_j) - v_t(r_k)| replaced by the sum), the
-// filter's error is below 2^-16.5 M (radius 2^-18.9, squares and fall speeds
-// 2^-17.8, the difference absolute in M) and the exact value's (binary64, or
-// binary32 with a 1-ulp cube root) below 2^-19 M, so pf + 2^-10 M + 2^-100 < u
-// implies p < u.  The filter abstains within 2^-14 of a terminal-velocity
-// regime boundary (radius error 2^-18.9) and when a binary32 value leaves
-// the normal range.
-__device__ __forceinline__ bool pair_certainly_zero(const PairConsts &C, float ratio_f, int64_t xi_j, double vj,
-                                                    double vk, uint32_t wa)
+// Binary32 image of a multiplicity, relative error < 2^-23.
+__device__ __forceinline__ float xi2f(int64_t x)
+{
+    return ((uint64_t)x >> 32) == 0 ? __uint2float_rz((uint32_t)x) : __ll2float_rz(x);
+}
+
+// Fall speed for the filter; clears ok within 2^-14 of a regime boundary,
+// where the filter's radius could fall on the other side of it.
+__device__ __forceinline__ float vt_guarded(const PairConsts &C, float r, bool &ok)
+{
+    if (r < C.r1_lo)
+        return C.k1f * (r * r);
+    if (r < C.r2_lo) {
+        ok &= r > C.r1_hi;
+        return C.k2f * r;
+    }
+    ok &= r > C.r2_hi;
+    return C.k3f * sqrtf(r);
+}
+
+// The collision count ceil(p - u) of a pair (xi_j >= xi_k > 0) when the
+// binary32 evaluation determines it, else -1 (before the cap at
+// floor(xi_j / xi_k)).  vj_hi, vk_hi: high words of the binary64 volumes.
+// With pf the filter's binary32 value of p and M a binary32 magnitude of all
+// of p's terms (K evaluated with |v_t(r_j) - v_t(r_k)| replaced by the sum),
+// the filter's error is below 2^-16.4 M (volumes 2^-20, radius 2^-18.8,
+// squares and fall speeds 2^-17.7, the difference absolute in M) and the
+// exact value's (binary64, or binary32 with a 1-ulp cube root) below
+// 2^-19 M.  So with E = 2^-10 M + 2^-100 and u in [u_lo, u_lo + 2^-23),
+// p - u lies in [pf - E - u_hi, pf + E - u_lo], and the bounds, widened by
+// the rounding of their own binary32 sums, pin ceil(p - u) when both fall in
+// one interval (m - 1, m].  The filter abstains within 2^-14 of a
+// terminal-velocity regime boundary (radius error 2^-18.8), when a binary32
+// value leaves the normal range, and for counts above 2^16.
+__device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float ratio_f, int64_t xi_j,
+                                                     uint32_t vj_hi, uint32_t vk_hi, uint32_t wa)
 {
     const float u_lo = uniform_lo23(wa);
-    bool in_j, in_k;
-    const float vjf = d2f_trunc(vj, in_j), vkf = d2f_trunc(vk, in_k);
-    const float xjf = xi_to_f32_rn(xi_j);
+    bool ok, ok_k;
+    const float vjf = hi2f(vj_hi, ok), vkf = hi2f(vk_hi, ok_k);
+    ok &= ok_k;
+    const float xjf = xi2f(xi_j);
     const float sc = C.dtdvf * ratio_f;
     float pf, mag;
-    bool ok = in_j & in_k;
     if (C.kernel == KERNEL_GOLOVIN) {
         const float K = C.bf * (vjf + vkf);
         pf = (K * xjf) * sc;
@@ -358,18 +386,42 @@ __device__ __forceinline__ bool pair_certainly_zero(const PairConsts &C, float r
         ok &= K >= 0x1p-126f;
     } else {
         const float rj = cbrt_filter(vjf * kVolToR3F), rk = cbrt_filter(vkf * kVolToR3F);
-        const float tj = vt_filter(C, rj), tk = vt_filter(C, rk);
+        const float tj = vt_guarded(C, rj, ok), tk = vt_guarded(C, rk, ok);
         const float s = rj + rk;
         const float a = kPiF * (s * s);
         const float K = a * fabsf(tj - tk);
         pf = (K * xjf) * sc;
         const float km = a * (tj + tk);
         mag = (km * xjf) * sc;
-        const float g1 = C.r1f * 0x1p-14f, g2 = C.r2f * 0x1p-14f;
-        ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f) && fabsf(rj - C.r1f) > g1 &&
-              fabsf(rk - C.r1f) > g1 && fabsf(rj - C.r2f) > g2 && fabsf(rk - C.r2f) > g2;
+        ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f);
     }
-    return ok && (pf + mag * 0x1p-10f + 0x1p-100f) < u_lo;
+    const float E = mag * 0x1p-10f + 0x1p-100f;
+    const float slack = (fabsf(pf) + E + 1.0f) * 0x1p-20f;
+    const float hi = ((pf + E) - u_lo) + slack;
+    if (ok && hi <= 0.0f)
+        return 0;
+    const float lo = ((pf - E) - (u_lo + 0x1p-23f)) - slack;
+    const float m = ceilf(hi);
+    if (!ok || ceilf(lo) != m || !(m <= 65536.0f))
+        return -1;
+    return (int32_t)m;
+}
+
+// The same from full binary64 volumes.
+__device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float ratio_f, int64_t xi_j, double vj,
+                                                     double vk, uint32_t wa)
+{
+    return pair_gamma_filter(C, ratio_f, xi_j, (uint32_t)__double2hiint(vj), (uint32_t)__double2hiint(vk), wa);
+}
+
+// gamma capped at floor(xi_j / xi_k) for a certain count g >= 1 (the
+// comparison of the definition, made exactly in integers: g is small).
+__device__ __forceinline__ int64_t cap_gamma(int32_t g, int64_t xi_j, int64_t xi_k)
+{
+    if (g == 1)
+        return 1; // xi_j >= xi_k
+    const int64_t q = xi_j / xi_k;
+    return (int64_t)g < q ? (int64_t)g : q;
 }
 
 // ------------------------------------------------------------ exact gamma
@@ -406,7 +458,9 @@ __device__ __forceinline__ int64_t pair_gamma_exact(const InstDev *P, uint32_t n
 // (the split case).
 __device__ __forceinline__ bool shima_update(int64_t gamma, int64_t &xi_j, int64_t &xi_k, double &vj, double &vk)
 {
-    const double vnew = __dadd_rn(vk, __dmul_rn(__ll2double_rn(gamma), vj));
+    // (double)1 * v_j is v_j exactly: one binary64 add for the common gamma = 1
+    const double t = gamma == 1 ? vj : __dmul_rn(__ll2double_rn(gamma), vj);
+    const double vnew = __dadd_rn(vk, t);
     const int64_t rem = xi_j - gamma * xi_k;
     if (rem > 0) {
         xi_j = rem;

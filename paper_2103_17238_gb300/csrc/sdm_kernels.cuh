@@ -131,6 +131,8 @@ struct QEntry {
     uint32_t wa, wb;         // the pair's uniform words
     uint32_t n_c;            // live SDs of its cell
     int32_t inst;            // its run
+    int32_t gamma;           // certain collision count (>= 1), or -1: evaluate exactly
+    int32_t pad_;
 };
 
 constexpr int kQueueFlush = 64; // flush once this many pairs wait
@@ -192,7 +194,8 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
         for (uint32_t e = t; e < nq; e += NT) {
             QEntry E = s_q[e];
             InstDev *Pq = insts[E.inst];
-            const int64_t g = pair_gamma_exact(Pq, E.n_c, E.xj, E.xk, E.vj, E.vk, E.wa, E.wb);
+            const int64_t g = E.gamma > 0 ? cap_gamma(E.gamma, E.xj, E.xk)
+                                          : pair_gamma_exact(Pq, E.n_c, E.xj, E.xk, E.vj, E.vk, E.wa, E.wb);
             if (g > 0) {
                 const bool split = shima_update(g, E.xj, E.xk, E.vj, E.vk);
                 Pq->xi[E.slot_j] = E.xj;
@@ -340,7 +343,8 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
                     }
                     double va = vs[a], vb = vs[b];
                     const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
-                    if (pair_certainly_zero(C, ratio_f, xa, va, vb, wa))
+                    const int32_t gf = pair_gamma_filter(C, ratio_f, xa, va, vb, wa);
+                    if (gf == 0)
                         continue;
                     const uint32_t qi = atomicAdd(&s_qn, 1u);
                     if (qi < QCAP) {
@@ -355,9 +359,11 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
                         E.wb = wb;
                         E.n_c = n_c;
                         E.inst = meta.w;
+                        E.gamma = gf;
                         s_q[qi] = E;
-                    } else { // queue full: evaluate here
-                        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                    } else { // queue full: update here
+                        const int64_t g = gf > 0 ? cap_gamma(gf, xa, xb)
+                                                 : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
                         if (g > 0) {
                             const bool split = shima_update(g, xa, xb, va, vb);
                             gxi[a] = xa;
@@ -391,6 +397,7 @@ struct WQEntry {
     uint32_t wa, wb;         // the pair's uniform words
     uint32_t n_c;            // live SDs of its cell
     int32_t inst;            // its run
+    int32_t gamma;           // certain collision count (>= 1), or -1: evaluate exactly
 };
 
 constexpr int kWarpQueue = 96;
@@ -464,7 +471,8 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             InstDev *Pq = insts[E.inst];
             int64_t xj = Pq->xi[E.slot_j], xk = Pq->xi[E.slot_k];
             double vj = Pq->v[E.slot_j], vk = Pq->v[E.slot_k];
-            const int64_t g = pair_gamma_exact(Pq, E.n_c, xj, xk, vj, vk, E.wa, E.wb);
+            const int64_t g = E.gamma > 0 ? cap_gamma(E.gamma, xj, xk)
+                                          : pair_gamma_exact(Pq, E.n_c, xj, xk, vj, vk, E.wa, E.wb);
             if (g > 0) {
                 const bool split = shima_update(g, xj, xk, vj, vk);
                 Pq->xi[E.slot_j] = xj;
@@ -590,10 +598,13 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             }
             __syncwarp();
 
+            // pairs (l = 2q, 2q + 1 share one Philox block): the filter
+            // settles most; colliding and undecided ones join the queue
             const uint32_t n_pairs = n_c / 2;
             const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
             const PairConsts C = pair_consts(P);
             const uint32_t n_q = (n_pairs + 1) / 2;
+            const uint32_t *vs_words = reinterpret_cast<const uint32_t *>(vs);
             for (uint32_t q0 = 0; q0 < n_q; q0 += 32) { // warp-uniform trip count
                 const uint32_t q = q0 + lane;
                 const uint4 w = draw4(seed, q, cell, s, 1u);
@@ -601,28 +612,23 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t l = 2 * q + h;
                     const bool valid = q < n_q && l < n_pairs;
-                    int a = 0, b = 0;
-                    int64_t xa = 0, xb = 0;
-                    double va = 0.0, vb = 0.0;
-                    bool und = false;
+                    uint32_t a = 0, b = 0;
+                    int32_t gf = 0;
                     const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
                     if (valid) {
-                        a = s_perm[2 * l];
-                        b = s_perm[2 * l + 1];
-                        xa = xs[a];
-                        xb = xs[b];
+                        const uint32_t ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
+                        a = ab & 0xFFFFu;
+                        b = ab >> 16;
+                        int64_t xa = xs[a], xb = xs[b];
                         if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
-                            const int tmp = a;
+                            const uint32_t tmp = a;
                             a = b;
                             b = tmp;
-                            const int64_t tx = xa;
                             xa = xb;
-                            xb = tx;
                         }
-                        va = vs[a];
-                        vb = vs[b];
-                        und = !pair_certainly_zero(C, ratio_f, xa, va, vb, wa);
+                        gf = pair_gamma_filter(C, ratio_f, xa, vs_words[2 * a + 1], vs_words[2 * b + 1], wa);
                     }
+                    const bool und = gf != 0;
                     const unsigned m = __ballot_sync(FULL, und);
                     if (m) {
                         const uint32_t base = s_qn;
@@ -630,15 +636,19 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                         if (und) {
                             if (idx < (uint32_t)kWarpQueue) {
                                 WQEntry E;
-                                E.slot_j = (uint32_t)(meta.x + a);
-                                E.slot_k = (uint32_t)(meta.x + b);
+                                E.slot_j = (uint32_t)(meta.x + (int)a);
+                                E.slot_k = (uint32_t)(meta.x + (int)b);
                                 E.wa = wa;
                                 E.wb = wb;
                                 E.n_c = n_c;
                                 E.inst = meta.w;
+                                E.gamma = gf;
                                 s_q[idx] = E;
-                            } else { // queue full: evaluate here
-                                const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                            } else { // queue full: update here
+                                int64_t xa = xs[a], xb = xs[b];
+                                double va = vs[a], vb = vs[b];
+                                const int64_t g = gf > 0 ? cap_gamma(gf, xa, xb)
+                                                         : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
                                 if (g > 0) {
                                     const bool split = shima_update(g, xa, xb, va, vb);
                                     gxi[a] = xa;
@@ -924,9 +934,10 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
         }
         double va = gv[a], vb = gv[b];
         const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
-        if (pair_certainly_zero(C, ratio_f, xa, va, vb, wa))
+        const int32_t gf = pair_gamma_filter(C, ratio_f, xa, va, vb, wa);
+        if (gf == 0)
             continue;
-        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+        const int64_t g = gf > 0 ? cap_gamma(gf, xa, xb) : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
         if (g > 0) {
             const bool split = shima_update(g, xa, xb, va, vb);
             gxi[a] = xa;
@@ -952,18 +963,26 @@ __global__ void advance_steps_kernel(InstDev *const *insts, int32_t n_inst, int6
 constexpr int kSpecNT = 256;
 constexpr int kMaxEdges = 1024;
 
-// One CTA per cell: live SDs binned by radius (the exact cube root, so the
-// bin of every SD is the one of the definition), sum(xi v) per bin.
+// One CTA per cell: live SDs binned by radius, sum(xi v) per bin.  The bin
+// of every SD is the one the exact cube root gives: a binary32 radius
+// (relative error below 2^-18.8) decides it when it lies more than 2^-14
+// from every bin edge, else the exact binary64 radius and search do.
 // per_cell: acc[cell * nb + b]; otherwise atomically into acc[b].
 __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__restrict__ P, const double *__restrict__ edges,
                                                            int32_t n_edges, int32_t per_cell, double *__restrict__ acc)
 {
     __shared__ double s_edges[kMaxEdges];
+    __shared__ float s_lo[kMaxEdges], s_hi[kMaxEdges]; // edges widened by 2^-14 either way
     __shared__ double s_acc[kMaxEdges];
     const int cell = blockIdx.x;
     const int nb = n_edges - 1;
-    for (int i = threadIdx.x; i < n_edges; i += kSpecNT)
-        s_edges[i] = edges[i];
+    for (int i = threadIdx.x; i < n_edges; i += kSpecNT) {
+        const double e = edges[i];
+        s_edges[i] = e;
+        const float ef = __double2float_rn(e);
+        s_lo[i] = ef * (1.0f - 0x1p-14f);
+        s_hi[i] = ef * (1.0f + 0x1p-14f);
+    }
     for (int i = threadIdx.x; i < nb; i += kSpecNT)
         s_acc[i] = 0.0;
     __syncthreads();
@@ -971,24 +990,43 @@ __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__rest
     const int n = P->cell_off[cell + 1] - off;
     const int64_t *gxi = P->xi + off;
     const double *gv = P->v + off;
-    const double e0 = s_edges[0], eN = s_edges[n_edges - 1];
     for (int i = threadIdx.x; i < n; i += kSpecNT) {
         const int64_t x = gxi[i];
         if (x <= 0)
             continue;
         const double v = gv[i];
-        const double r = radius_exact(v);
-        if (r < e0 || !(r < eN))
-            continue;
-        int lo = 0, hi = n_edges - 1;
+        bool in_range;
+        const float rf = cbrt_filter(hi2f((uint32_t)__double2hiint(v), in_range) * kVolToR3F);
+        // largest lo with lower(edge[lo]) <= rf
+        int lo = -1, hi = n_edges;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (s_edges[mid] <= r)
+            if (s_lo[mid] <= rf)
                 lo = mid;
             else
                 hi = mid;
         }
-        atomicAdd(&s_acc[lo], __dmul_rn(__ll2double_rn(x), v));
+        int bin;
+        const bool clear_below = lo >= 0 && rf > s_hi[lo];
+        const bool clear_above = lo + 1 >= n_edges || rf < s_lo[lo + 1];
+        if (in_range && (lo < 0 || clear_below) && clear_above) {
+            bin = (lo < 0 || lo >= nb) ? -1 : lo; // outside [e_0, e_N): dropped
+        } else {
+            const double r = radius_exact(v);
+            if (r < s_edges[0] || !(r < s_edges[n_edges - 1]))
+                continue;
+            int a = 0, z = n_edges - 1;
+            while (z - a > 1) {
+                const int mid = (a + z) >> 1;
+                if (s_edges[mid] <= r)
+                    a = mid;
+                else
+                    z = mid;
+            }
+            bin = a;
+        }
+        if (bin >= 0)
+            atomicAdd(&s_acc[bin], __dmul_rn(__ll2double_rn(x), v));
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += kSpecNT) {

@@ -126,6 +126,29 @@ def test_ragged_cells_every_class(env, kernel, precision, dv):
     run.close()
 
 
+@pytest.mark.parametrize("kernel", ["golovin", "geometric"])
+@pytest.mark.parametrize("precision", ["fp64", "kfp32"])
+def test_probability_sweep(env, kernel, precision):
+    """p from ~1e-3 to ~1e3 (dV over six decades): gamma = 0, 1, several,
+    capped at floor(xi_j / xi_k), and counts whose p - u lies near an
+    integer, across the 64/128/256-SD warp classes and a 512-SD block class."""
+    O, sdm, torch = env
+    rng = np.random.default_rng(99)
+    sizes = [64, 128, 256, 512, 200, 90]
+    for dv in (1e3, 1e1, 1e-1, 1e-3):
+        n = sum(sizes)
+        cell = np.repeat(np.arange(len(sizes), dtype=np.int32), sizes)
+        xi = rng.integers(1, 10**7, n).astype(np.int64)
+        xi[rng.random(n) < 0.2] = 5000
+        r = np.exp(rng.uniform(np.log(3e-6), np.log(1e-3), n))
+        v = 4 / 3 * np.pi * r**3
+        run = _gpu_run(sdm, kernel, precision, xi, v, cell, len(sizes), dv, 123, 8, chunks=[3, 5])
+        gx, gv = run.attributes()
+        st = _oracle_run(O, kernel, precision, xi, v, cell, len(sizes), dv, 123, 8)
+        _assert_same(gx, gv, st, f"sweep {kernel} {precision} dv={dv}")
+        run.close()
+
+
 def test_terminal_velocity_regime_edges(env):
     """Radii within a few ulp of the Rogers-Yau boundaries, where the binary32
     filter must abstain."""
@@ -143,6 +166,32 @@ def test_terminal_velocity_regime_edges(env):
         st = _oracle_run(O, "geometric", prec, xi, v, cell, 8, 1e-3, 21, 6)
         _assert_same(gx, gv, st, f"regime edges {prec}")
         run.close()
+
+
+def test_spectrum_bin_edges(env):
+    """Radii on, just below and just above every bin edge (relative 1e-15 ..
+    1e-5): the binary32 radius must defer to the exact one there, so every SD
+    lands in the bin of the definition."""
+    O, sdm, torch = env
+    e = I.R_EDGES
+    rs = []
+    for x in e:
+        for d in (0.0, 1e-15, -1e-15, 1e-12, -1e-12, 1e-9, -1e-9, 1e-6, -1e-6, 6e-5, -6e-5):
+            rs.append(x * (1.0 + d))
+    r = np.array(rs)
+    v = 4.0 / 3.0 * np.pi * r**3
+    n = len(v) + (len(v) % 2)
+    v = np.resize(v, n)
+    xi = np.arange(1, n + 1, dtype=np.int64) * 1000
+    cell = (np.arange(n) % 4).astype(np.int32)
+    run = sdm.Run(sdm.make_config("golovin", dv=1e3, n_cells=4), n).set_attributes(xi, v, cell)
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, 4)
+    P = O.params("golovin", dv=1e3)
+    got = run.spectrum(e, per_cell=True)
+    want = O.spectrum(P, st, e, per_cell=True)
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+    assert np.array_equal(got > 0, want > 0)
+    run.close()
 
 
 def test_big_cell_path(env):
