@@ -124,6 +124,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def max_over_ranks(t_local: float, dist=None, device=None) -> float:
+    """The slowest rank's timed seconds (the whole job ends with it)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_local
+    import torch
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(pairs_per_replica_step: float, steps: int, world: int, t_max: float) -> float:
+    """Pair-updates per second of all replicas together (weak scaling: every
+    rank steps its own replica of the workload)."""
+    return pairs_per_replica_step * steps * world / t_max
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank's replica draws its own random streams."""
+    return rank
+
+
 def pairs_per_step(xi: np.ndarray, cell: np.ndarray, n_cells: int) -> int:
     live = np.bincount(cell[xi > 0], minlength=n_cells)
     return int((live // 2).sum())
@@ -141,7 +163,7 @@ def run_ours(args, rank: int, world: int):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    g = I.grid_geometric(seed=rank)
+    g = I.grid_geometric(seed=replica_seed(rank))
     n_sd, n_cells = g.n_sd, g.n_cells
     cfg = lambda: sdm.make_config("geometric", "fp64", dv=g.dv, n_cells=n_cells, seed=g.seed)
     pairs0 = pairs_per_step(g.xi, g.cell, n_cells)
@@ -208,13 +230,8 @@ def run_ours(args, rank: int, world: int):
     pairs_avg = 0.5 * (pairs0 + pairs_end)
     total_ms = sum(step_ms) + sum(spec_ms)
     t_local = total_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = pairs_avg * K * world / t_max
+    t_max = max_over_ranks(t_local, dist if world > 1 else None, dev)
+    value = whole_job_value(pairs_avg, K, world, t_max)
 
     # writes per step (untimed replay of the same steps, counting changed SDs)
     written = count_written_bytes(run_factory=fresh_run, steps=min(K, RUN_STEPS), torch=torch, sdm=sdm,
