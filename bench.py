@@ -332,20 +332,35 @@ def _timed(torch, fn):
 
 def measure_batched_vs_plain(sdm, torch, steps=20):
     """1024 Golovin boxes, n_sd = round(2^U(8,16)): one fused batch (CUDA graph)
-    against one context stepped after another.  FP64 states of both forms are
-    identical bit for bit (checked), so accuracy is equal by construction.
-    State (~12M SDs, ~190 MB) exceeds L2; no flush needed."""
+    against one context stepped after another.  The batch runs once with the
+    default launch tuning and once with the autotuner's pick (timed on a
+    separate copy of the ensemble).  FP64 states of all forms are identical
+    bit for bit (checked), so accuracy is equal by construction.  State (~12M
+    SDs, ~190 MB) exceeds L2; no flush needed."""
+    from paper_2103_17238_gb300 import autotune
+
     insts = I.batched_ensemble(steps=steps)
     pairs = sum(pairs_per_step(t.xi, t.cell, t.n_cells) for t in insts)
     mk = lambda t: sdm.Run(sdm.make_config("golovin", dv=t.dv, seed=t.seed), t.n_sd).set_attributes(
         t.xi, t.v, t.cell)
+    probe = [mk(t) for t in insts]
+    rep = autotune.tune(probe, steps=3, cache_path=None)
+    for r in probe:
+        r.close()
+    best = rep["best"]
+
     runs_b = [mk(t) for t in insts]
     runs_p = [mk(t) for t in insts]
-    batch = sdm.Batch(runs_b, use_graph=True, graph_steps=10)
-    batch.step(10)  # warm-up (captures the graph)
+    times = {}
+    for name, tuning in (("default", None), ("tuned", best)):
+        sdm.sdm_set_tuning(tuning)
+        batch = sdm.Batch(runs_b, use_graph=True, graph_steps=10)
+        batch.step(10)  # warm-up (captures the graph)
+        times[name] = _timed(torch, lambda: batch.step(steps))
+        batch.close()
+    # plain contexts build their plans at their first step: with the pick
     for r in runs_p:
         r.step(10)
-    tb = _timed(torch, lambda: batch.step(steps))
 
     def plain():
         for _ in range(steps):
@@ -353,14 +368,22 @@ def measure_batched_vs_plain(sdm, torch, steps=20):
                 r.step(1)
 
     tp = _timed(torch, plain)
-    same = all(np.array_equal(a.attributes()[0], b.attributes()[0]) for a, b in zip(runs_b[:64], runs_p[:64]))
-    batch.close()
+    for r in runs_p:
+        r.step(10 + steps)
+    sdm.sdm_set_tuning(None)
+    same = all(np.array_equal(a.attributes()[0], b.attributes()[0]) and
+               np.array_equal(a.attributes()[1], b.attributes()[1]) for a, b in zip(runs_b[:64], runs_p[:64]))
     for r in runs_b + runs_p:
         r.close()
+    tb = times["tuned"]
     return {"workload": "1024 Golovin boxes, n_sd=round(2^U(8,16)) (rng 3), seeds 0..1023, FP64",
             "sd_total": int(sum(t.n_sd for t in insts)), "steps": steps,
-            "batched_pair_updates_per_s": pairs * steps / tb, "plain_pair_updates_per_s": pairs * steps / tp,
-            "speedup": tp / tb, "equal_accuracy": "bit-identical states" if same else "MISMATCH"}
+            "batched_pair_updates_per_s": pairs * steps / tb,
+            "batched_default_tuning_pair_updates_per_s": pairs * steps / times["default"],
+            "plain_pair_updates_per_s": pairs * steps / tp,
+            "speedup": tp / tb, "autotune": {"best": best, "candidates": rep["candidates"],
+                                             "tuning_s": round(rep["tuning_s"], 2)},
+            "equal_accuracy": "bit-identical states" if same else "MISMATCH"}
 
 
 def measure_large_cells(sdm, torch, steps=10, members=32):

@@ -193,6 +193,25 @@ sdm_status sdm_batch_destroy(sdm_batch *batch);
 
 const char *sdm_batch_last_error(const sdm_batch *batch);
 
+/* ---- launch tuning.  Which cells are sorted in shared memory (the rest take
+ * the multi-pass global path), which run one warp per cell, and how many
+ * warps share a block.  Results never depend on it: every setting gives the
+ * same state bit for bit.  Process-wide; applies to contexts and batches
+ * whose launch plans are built after the call (a context builds its plan at
+ * its first sdm_coalescence_step after sdm_set_attributes, a batch at
+ * sdm_batch_create).  paper_2103_17238_gb300/autotune.py times candidates
+ * and sets the fastest. */
+typedef struct sdm_tuning {
+    int32_t smem_max_sd;     /* largest cell sorted in shared memory: 512, 1024, 2048 or 4096 (default) */
+    int32_t warp_cell_max;   /* largest cell run by one warp: 0, 64, 128 or 256 (default), <= smem_max_sd */
+    int32_t warps_per_block; /* warps per block of the warp-per-cell kernel: 1, 2 (default) or 4 */
+    int32_t reserved0;       /* must be 0 */
+} sdm_tuning;
+
+/* NULL restores the defaults.  Errors: SDM_EINVAL. */
+sdm_status sdm_set_tuning(const sdm_tuning *tuning);
+sdm_status sdm_get_tuning(sdm_tuning *out);
+
 /* ---- allocation-free step of one cell.  This call has no counterpart in
  * the paper; it exists for callers that cannot allocate device memory while
  * they run: a host model that reserves all of its GPU memory up front in its

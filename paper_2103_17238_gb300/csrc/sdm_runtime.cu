@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -60,13 +61,13 @@ struct Buf {
 // Cell-size classes of the shared-memory path.
 constexpr int kClassCap[] = {64, 128, 256, 512, 1024, 2048, 4096};
 constexpr int kNumClass = sizeof(kClassCap) / sizeof(kClassCap[0]);
-constexpr int kSmemMaxCell = 4096;
 
 struct Plan {
     int n_inst = 0;
     InstDev **d_insts = nullptr; // table of the runs' device records
     WorkItem *d_items[kNumClass] = {};
     int n_items[kNumClass] = {};
+    int variant[kNumClass] = {};
     BigCell *d_bigs = nullptr;
     int n_big = 0;
     BigChunk *d_chunks = nullptr;
@@ -189,20 +190,68 @@ int big_lb(int n)
 
 size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
 
-// Shared-memory classes.  Up to 256 SDs: one warp per cell (capacity,
-// warps per block, pipeline stages); larger: one block per cell (capacity,
-// threads, stages).
-#define SDM_WARP_CLASSES(X)                                                                                            \
-    X(0, 64, 4, 2)                                                                                                     \
-    X(1, 128, 4, 2)                                                                                                    \
-    X(2, 256, 2, 2)
-#define SDM_CELL_CLASSES(X)                                                                                            \
-    X(3, 512, 256, 4)                                                                                                  \
-    X(4, 1024, 512, 3)                                                                                                 \
-    X(5, 2048, 1024, 2)                                                                                                \
-    X(6, 4096, 1024, 2)
+// Kernel variants of the shared-memory path.  Warp-per-cell kernels for cells
+// of up to 256 SDs (capacity, warps per block; 2 pipeline stages); block-per-
+// cell kernels for every class (capacity, threads, stages).  The launch
+// tuning (sdm_set_tuning) picks one variant per size class when a plan is
+// built.
+#define SDM_WARP_VARIANTS(X)                                                                                           \
+    X(64, 1) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(128, 4) X(256, 1) X(256, 2) X(256, 4)
+#define SDM_BLOCK_VARIANTS(X)                                                                                          \
+    X(64, 32, 4) X(128, 64, 4) X(256, 128, 4) X(512, 256, 4) X(1024, 512, 3) X(2048, 1024, 2) X(4096, 1024, 2)
 
-int g_cell_grid[kNumClass]; // persistent blocks per class (resident blocks x SMs)
+typedef void (*launch_fn)(int grid, int n, const WorkItem *, InstDev *const *, int64_t, cudaStream_t);
+
+template <int CAP, int WARPS>
+void launch_warp(int grid, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
+{
+    warp_cell_step_kernel<CAP, WARPS, 2><<<grid, 32 * WARPS, WarpSmem<CAP, 2>::per_warp * WARPS, st>>>(items, n, insts,
+                                                                                                     off);
+}
+
+template <int CAP, int NT, int ST>
+void launch_block(int grid, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
+{
+    cell_step_kernel<CAP, NT, ST><<<grid, NT, CellSmem<CAP, ST>::bytes, st>>>(items, n, insts, off);
+}
+
+struct Variant {
+    int cap;
+    int warps; // warps per block of the warp kernel; 0: block kernel
+    launch_fn launch;
+    int max_grid; // resident blocks x SMs (set at configuration)
+};
+
+Variant g_variants[] = {
+#define X(CAP, WARPS) {CAP, WARPS, launch_warp<CAP, WARPS>, 0},
+    SDM_WARP_VARIANTS(X)
+#undef X
+#define X(CAP, NT, ST) {CAP, 0, launch_block<CAP, NT, ST>, 0},
+        SDM_BLOCK_VARIANTS(X)
+#undef X
+};
+constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
+
+std::mutex g_tuning_mutex;
+sdm_tuning g_tuning = {4096, 256, 2, 0};
+
+sdm_tuning current_tuning()
+{
+    std::lock_guard<std::mutex> lock(g_tuning_mutex);
+    return g_tuning;
+}
+
+int variant_for(int cap, const sdm_tuning &t)
+{
+    for (int v = 0; v < kNumVariants; ++v) {
+        const Variant &x = g_variants[v];
+        if (x.cap != cap)
+            continue;
+        if (cap <= t.warp_cell_max ? x.warps == t.warps_per_block : x.warps == 0)
+            return v;
+    }
+    return -1;
+}
 
 cudaError_t configure_kernels_once()
 {
@@ -213,21 +262,22 @@ cudaError_t configure_kernels_once()
             return r;
         if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return r;
-#define X(IDX, CAP, WARPS, ST)                                                                                         \
+        int v = 0;
+#define X(CAP, WARPS)                                                                                                  \
     {                                                                                                                  \
-        const int bytes = (int)(WarpSmem<CAP, ST>::per_warp * WARPS);                                                  \
-        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, WARPS, ST>,                                           \
+        const int bytes = (int)(WarpSmem<CAP, 2>::per_warp * WARPS);                                                   \
+        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, WARPS, 2>,                                            \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)             \
             e = r;                                                                                                     \
         int per_sm = 0;                                                                                                \
-        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, WARPS, ST>,         \
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, WARPS, 2>,          \
                                                                32 * WARPS, bytes)) != cudaSuccess)                     \
             e = r;                                                                                                     \
-        g_cell_grid[IDX] = std::max(1, per_sm) * sms;                                                                  \
+        g_variants[v++].max_grid = std::max(1, per_sm) * sms;                                                          \
     }
-        SDM_WARP_CLASSES(X)
+        SDM_WARP_VARIANTS(X)
 #undef X
-#define X(IDX, CAP, NT, ST)                                                                                            \
+#define X(CAP, NT, ST)                                                                                                 \
     {                                                                                                                  \
         const int bytes = (int)CellSmem<CAP, ST>::bytes;                                                               \
         if ((r = cudaFuncSetAttribute(cell_step_kernel<CAP, NT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
@@ -237,9 +287,9 @@ cudaError_t configure_kernels_once()
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_step_kernel<CAP, NT, ST>, NT, bytes)) != \
             cudaSuccess)                                                                                               \
             e = r;                                                                                                     \
-        g_cell_grid[IDX] = std::max(1, per_sm) * sms;                                                                  \
+        g_variants[v++].max_grid = std::max(1, per_sm) * sms;                                                          \
     }
-        SDM_CELL_CLASSES(X)
+        SDM_BLOCK_VARIANTS(X)
 #undef X
         const int hb = (int)big_hist_smem(kBigMaxLB);
         if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
@@ -250,34 +300,20 @@ cudaError_t configure_kernels_once()
     return status;
 }
 
-void launch_cell_class(int cls, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
+void launch_variant(int v, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
 {
-    switch (cls) {
-#define X(IDX, CAP, WARPS, ST)                                                                                         \
-    case IDX: {                                                                                                        \
-        const int grid = std::min((n + WARPS - 1) / WARPS, g_cell_grid[IDX]);                                          \
-        warp_cell_step_kernel<CAP, WARPS, ST>                                                                          \
-            <<<grid, 32 * WARPS, WarpSmem<CAP, ST>::per_warp * WARPS, st>>>(items, n, insts, off);                     \
-        break;                                                                                                         \
-    }
-        SDM_WARP_CLASSES(X)
-#undef X
-#define X(IDX, CAP, NT, ST)                                                                                            \
-    case IDX: {                                                                                                        \
-        const int grid = std::min(n, g_cell_grid[IDX]);                                                                \
-        cell_step_kernel<CAP, NT, ST><<<grid, NT, CellSmem<CAP, ST>::bytes, st>>>(items, n, insts, off);               \
-        break;                                                                                                         \
-    }
-        SDM_CELL_CLASSES(X)
-#undef X
-    }
+    const Variant &x = g_variants[v];
+    const int per_block = x.warps > 0 ? x.warps : 1;
+    const int grid = std::min((n + per_block - 1) / per_block, x.max_grid);
+    x.launch(grid, n, items, insts, off, st);
 }
 
-int class_of(int n)
+// Size class of a cell of n stored SDs under the tuning; -1: multi-pass path.
+int class_of(int n, const sdm_tuning &t)
 {
     for (int c = 0; c < kNumClass; ++c)
         if (n <= kClassCap[c])
-            return c;
+            return kClassCap[c] <= t.smem_max_sd ? c : -1;
     return -1;
 }
 
@@ -294,6 +330,9 @@ sdm_status build_plan(sdm_batch *b)
     std::vector<BigPairs> pairs;
     std::vector<InstDev *> insts(n_inst);
     int64_t hist_total = 0, sd_total = 0, bkt_total = 0;
+    const sdm_tuning tun = current_tuning();
+    for (int k = 0; k < kNumClass; ++k)
+        pl.variant[k] = variant_for(kClassCap[k], tun);
     for (int i = 0; i < n_inst; ++i) {
         sdm_ctx *c = b->ctxs[i];
         insts[i] = c->d_inst;
@@ -301,7 +340,7 @@ sdm_status build_plan(sdm_batch *b)
             const int n = c->h_cell_off[cell + 1] - c->h_cell_off[cell];
             if (n < 2)
                 continue;
-            const int cls = class_of(n);
+            const int cls = class_of(n, tun);
             if (cls >= 0) {
                 items[cls].push_back(WorkItem{i, cell});
                 continue;
@@ -387,7 +426,7 @@ void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
 {
     for (int k = 0; k < kNumClass; ++k)
         if (pl.n_items[k])
-            launch_cell_class(k, pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
+            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
     if (pl.n_big) {
         const size_t hs = big_hist_smem(pl.max_big_lb);
         big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
@@ -635,7 +674,7 @@ int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t larges
 {
     const int64_t slots = capacity_sd + n_cells;
     int64_t bytes = slots * (8 + 8 + 4) + ((int64_t)n_cells + 1) * 4 + (int64_t)sizeof(InstDev);
-    if (largest_cell > kSmemMaxCell) {
+    if (largest_cell > current_tuning().smem_max_sd) {
         // big-cell scratch, at most: keys, ranks, perm per SD; counts per chunk and bucket
         const int lb = big_lb(largest_cell);
         const int64_t chunks = (capacity_sd + kBigChunk - 1) / kBigChunk + n_cells;
@@ -983,6 +1022,34 @@ sdm_status sdm_batch_destroy(sdm_batch *batch)
     delete batch;
     if (e != cudaSuccess)
         return fail(nullptr, SDM_ECUDA, "sdm_batch_destroy: %s", cudaGetErrorString(e));
+    return SDM_OK;
+}
+
+sdm_status sdm_set_tuning(const sdm_tuning *t)
+{
+    sdm_tuning v = {4096, 256, 2, 0};
+    if (t) {
+        const bool smem_ok = t->smem_max_sd == 512 || t->smem_max_sd == 1024 || t->smem_max_sd == 2048 ||
+                             t->smem_max_sd == 4096;
+        const bool warp_ok = t->warp_cell_max == 0 || t->warp_cell_max == 64 || t->warp_cell_max == 128 ||
+                             t->warp_cell_max == 256;
+        const bool wpb_ok = t->warps_per_block == 1 || t->warps_per_block == 2 || t->warps_per_block == 4;
+        if (!smem_ok || !warp_ok || !wpb_ok || t->reserved0 != 0 || t->warp_cell_max > t->smem_max_sd)
+            return fail(nullptr, SDM_EINVAL,
+                        "tuning: smem_max_sd in {512,1024,2048,4096}, warp_cell_max in {0,64,128,256} and <= "
+                        "smem_max_sd, warps_per_block in {1,2,4}, reserved0 = 0");
+        v = *t;
+    }
+    std::lock_guard<std::mutex> lock(g_tuning_mutex);
+    g_tuning = v;
+    return SDM_OK;
+}
+
+sdm_status sdm_get_tuning(sdm_tuning *out)
+{
+    if (!out)
+        return fail(nullptr, SDM_EINVAL, "out is NULL");
+    *out = current_tuning();
     return SDM_OK;
 }
 

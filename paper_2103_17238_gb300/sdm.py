@@ -29,7 +29,7 @@ EXPORTS = [
     "sdm_config_default", "sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
     "sdm_get_attributes", "sdm_get_info", "sdm_footprint_bytes", "sdm_destroy", "sdm_last_error",
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
-    "sdm_cell_step_noalloc",
+    "sdm_cell_step_noalloc", "sdm_set_tuning", "sdm_get_tuning",
 ]
 NOALLOC_MAX_SD = 1 << 20
 
@@ -63,6 +63,15 @@ class sdm_config(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class sdm_tuning(ctypes.Structure):
+    _fields_ = [
+        ("smem_max_sd", ctypes.c_int32),
+        ("warp_cell_max", ctypes.c_int32),
+        ("warps_per_block", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -112,9 +121,12 @@ def load(path: str = LIB_PATH):
         L.sdm_batch_last_error.argtypes = [vp]
         L.sdm_batch_last_error.restype = ctypes.c_char_p
         L.sdm_cell_step_noalloc.argtypes = [P(sdm_config), i64, vp, vp, i64, vp]
+        L.sdm_set_tuning.argtypes = [P(sdm_tuning)]
+        L.sdm_get_tuning.argtypes = [P(sdm_tuning)]
         for name in ("sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
                      "sdm_get_attributes", "sdm_get_info", "sdm_destroy", "sdm_batch_create",
-                     "sdm_batch_step", "sdm_batch_destroy", "sdm_cell_step_noalloc"):
+                     "sdm_batch_step", "sdm_batch_destroy", "sdm_cell_step_noalloc", "sdm_set_tuning",
+                     "sdm_get_tuning"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -284,6 +296,21 @@ def sdm_cell_step_noalloc(cfg: sdm_config, step: int, xi, volume, stream: int):
         raise ValueError("xi and volume must be contiguous (the step works in place)")
     _check(load().sdm_cell_step_noalloc(ctypes.byref(cfg), int(step), px, pv, int(kx.shape[0]),
                                         ctypes.c_void_p(stream)), "sdm_cell_step_noalloc")
+
+
+def sdm_set_tuning(tuning=None):
+    """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block; None: defaults."""
+    if tuning is None:
+        _check(load().sdm_set_tuning(None), "sdm_set_tuning")
+        return
+    t = sdm_tuning(int(tuning["smem_max_sd"]), int(tuning["warp_cell_max"]), int(tuning["warps_per_block"]), 0)
+    _check(load().sdm_set_tuning(ctypes.byref(t)), "sdm_set_tuning")
+
+
+def sdm_get_tuning() -> dict:
+    t = sdm_tuning()
+    _check(load().sdm_get_tuning(ctypes.byref(t)), "sdm_get_tuning")
+    return {"smem_max_sd": t.smem_max_sd, "warp_cell_max": t.warp_cell_max, "warps_per_block": t.warps_per_block}
 
 
 # ------------------------------------------------------------ owners

@@ -49,7 +49,7 @@ def test_ctypes_layout_matches_the_header(tmp_path):
     from paper_2103_17238_gb300 import sdm
 
     prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "sdm.h"', 'int main(void){']
-    for st in (sdm.sdm_config, sdm.sdm_info):
+    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning):
         name = st.__name__
         prog.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in st._fields_:
@@ -61,7 +61,7 @@ def test_ctypes_layout_matches_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                        check=True).stdout.splitlines())
-    for st in (sdm.sdm_config, sdm.sdm_info):
+    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning):
         assert int(out[st.__name__]) == ctypes.sizeof(st)
         for f, _ in st._fields_:
             assert int(out[f"{st.__name__}.{f}"]) == getattr(st, f).offset, f
@@ -89,3 +89,59 @@ def test_destroy_null_and_footprint(lib):
     assert small == (4096 + 1) * 20 + 2 * 4 + sdm.sdm_footprint_bytes(0, 1, 0) - (1 * 20 + 2 * 4)
     big = sdm.sdm_footprint_bytes(2**20, 1, 2**20)
     assert big > 2**20 * 20 + 2**20 * 16
+
+
+def test_tuning_round_trip_and_validation(lib):
+    """The launch tuning is host state: set, read back, rejected when out of
+    range (the previous setting stays), restored by NULL."""
+    from paper_2103_17238_gb300 import sdm
+
+    default = {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2}
+    sdm.sdm_set_tuning(None)
+    assert sdm.sdm_get_tuning() == default
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4}
+    sdm.sdm_set_tuning(t)
+    assert sdm.sdm_get_tuning() == t
+    for bad in ({"smem_max_sd": 8192, "warp_cell_max": 256, "warps_per_block": 2},
+                {"smem_max_sd": 1000, "warp_cell_max": 256, "warps_per_block": 2},
+                {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2},
+                {"smem_max_sd": 4096, "warp_cell_max": 96, "warps_per_block": 2},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 3},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 0}):
+        with pytest.raises(sdm.SdmError) as e:
+            sdm.sdm_set_tuning(bad)
+        assert e.value.status == sdm.SDM_EINVAL
+        assert sdm.sdm_get_tuning() == t
+    raw = sdm.sdm_tuning(4096, 256, 2, 1)  # reserved field must be zero
+    assert lib.sdm_set_tuning(ctypes.byref(raw)) == sdm.SDM_EINVAL
+    assert lib.sdm_get_tuning(None) == sdm.SDM_EINVAL
+    # cells above the shared-memory threshold need multi-pass scratch
+    assert sdm.sdm_footprint_bytes(4096, 1, 2048) > sdm.sdm_footprint_bytes(4096, 1, 1024)
+    sdm.sdm_set_tuning(None)
+    assert sdm.sdm_footprint_bytes(4096, 1, 2048) == sdm.sdm_footprint_bytes(4096, 1, 1024)
+
+
+def test_autotune_candidates_are_valid_and_signature_is_stable(lib):
+    from paper_2103_17238_gb300 import autotune, sdm
+
+    seen = set()
+    for c in autotune.CANDIDATES:
+        sdm.sdm_set_tuning(c)
+        seen.add(tuple(sorted(c.items())))
+    sdm.sdm_set_tuning(None)
+    assert len(seen) == len(autotune.CANDIDATES)
+    assert {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2} in autotune.CANDIDATES
+
+    class FakeRun:
+        def __init__(self, kernel, n_cells, largest):
+            self.cfg = sdm.make_config(kernel, "fp64", n_cells=n_cells)
+            self._info = sdm.sdm_info(n_sd=n_cells * largest, capacity_sd=n_cells * largest, step=0,
+                                      device_bytes=0, n_cells=n_cells, largest_cell=largest)
+
+        def info(self):
+            return self._info
+
+    a = autotune.signature([FakeRun("golovin", 1000, 200), FakeRun("geometric", 64, 3000)])
+    b = autotune.signature([FakeRun("golovin", 1100, 250), FakeRun("geometric", 60, 2900)])
+    c = autotune.signature([FakeRun("golovin", 1000, 600)])
+    assert a == b and a != c

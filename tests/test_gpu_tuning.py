@@ -1,0 +1,110 @@
+"""The launch tuning changes how cells are mapped to kernels, never the
+result: every setting must give the oracle's state bit for bit, for cells of
+every size class (and the multi-pass path above the shared-memory
+threshold), alone and in a batch; the autotuner picks one of its candidates
+and caches it."""
+import itertools
+import json
+
+import numpy as np
+import pytest
+
+from paper_2103_17238_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 2, 3, 31, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 1023, 1025, 2047, 2049, 4095,
+         4096, 4097, 6000]
+
+TUNINGS = [dict(smem_max_sd=s, warp_cell_max=w, warps_per_block=k)
+           for s, w, k in itertools.product((512, 1024, 2048, 4096), (0, 64, 128, 256), (1, 2, 4))
+           if not (w == 0 and k != 2)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from paper_2103_17238_gb300 import build as B
+    from paper_2103_17238_gb300 import sdm
+
+    B.build()
+    O.build()
+    torch.cuda.set_device(0)
+    yield O, sdm, torch
+    sdm.sdm_set_tuning(None)
+
+
+def _state(seed):
+    rng = np.random.default_rng(seed)
+    cells = np.concatenate([np.full(n, c, np.int32) for c, n in enumerate(SIZES)])
+    n = len(cells)
+    xi = np.where(rng.random(n) < 0.3, 1000, rng.integers(1, 10**9, n)).astype(np.int64)
+    xi[rng.random(n) < 0.05] = 0
+    r = np.exp(rng.uniform(np.log(2e-6), np.log(2e-3), n))
+    v = 4 / 3 * np.pi * r**3
+    perm = rng.permutation(n)
+    return xi[perm], v[perm], cells[perm]
+
+
+@pytest.mark.parametrize("kernel,precision", [("geometric", "fp64"), ("golovin", "kfp32")])
+def test_every_tuning_gives_the_oracle_state(env, kernel, precision):
+    O, sdm, torch = env
+    xi, v, cell = _state(23)
+    nc, dv, seed, steps = len(SIZES), 1e3, 31, 4
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, nc)
+    O.run(O.params(kernel, precision, dv=dv, seed=seed), st, 0, steps)
+    for t in TUNINGS:
+        sdm.sdm_set_tuning(t)
+        run = sdm.Run(sdm.make_config(kernel, precision, dv=dv, n_cells=nc, seed=seed), len(xi))
+        run.set_attributes(xi, v, cell).step(steps)
+        gx, gv = run.attributes()
+        run.close()
+        bad = np.nonzero(gx != st.xi)[0]
+        assert bad.size == 0, f"{t}: {bad.size} multiplicities differ"
+        assert np.array_equal(gv, st.v), f"{t}: volumes differ"
+    sdm.sdm_set_tuning(None)
+
+
+def test_autotuned_batch_equals_default(env, tmp_path):
+    O, sdm, torch = env
+    from paper_2103_17238_gb300 import autotune
+
+    specs = [I.box_golovin(3000, seed=1), I.grid_geometric(side=3, sd_per_cell=256, seed=2),
+             I.grid_geometric(side=2, sd_per_cell=1500, seed=3)]
+
+    def make():
+        return [sdm.Run(sdm.make_config("golovin" if g.n_cells == 1 else "geometric", dv=1e3, n_cells=g.n_cells,
+                                        seed=g.seed), g.n_sd).set_attributes(g.xi, g.v, g.cell) for g in specs]
+
+    sdm.sdm_set_tuning(None)
+    ref = make()
+    b = sdm.Batch(ref)
+    b.step(6)
+    torch.cuda.synchronize()
+    b.close()
+
+    cands = TUNINGS[::5]
+    cache = str(tmp_path / "tune.json")
+    probe = make()
+    rep = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
+    assert not rep["cached"] and rep["best"] in cands
+    assert sdm.sdm_get_tuning() == rep["best"]
+    assert rep["ms_per_step"] <= rep["worst_ms_per_step"]
+    again = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
+    assert again["cached"] and again["best"] == rep["best"]
+    assert rep["key"] in json.load(open(cache))
+
+    runs = make()
+    b = sdm.Batch(runs, use_graph=True, graph_steps=3)
+    b.step(6)
+    torch.cuda.synchronize()
+    b.close()
+    for r, a in zip(runs, ref):
+        x1, v1 = r.attributes()
+        x2, v2 = a.attributes()
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+    sdm.sdm_set_tuning(None)
