@@ -404,10 +404,29 @@ constexpr int kWarpQueue = 96;
 
 template <int CAP, int STAGES>
 struct WarpSmem {
-    // per warp: STAGES x (xi, v), key, bucket, rank, perm, queue
+    // per warp: STAGES x (xi, v), sort word, bucket, perm, queue
     static constexpr size_t per_warp =
-        (size_t)CAP * (16 * STAGES + 8 + 4 + 2 + 2) + sizeof(WQEntry) * (size_t)kWarpQueue;
+        (size_t)CAP * (16 * STAGES + 4 + 4 + 2) + sizeof(WQEntry) * (size_t)kWarpQueue;
 };
+
+// Position, among the n words of one bucket, of the SD of rank rk in full
+// (key, rank) order; the keys are drawn again.  Taken only by buckets in
+// which two keys share their top 24 bits (about one cell in 500 at 256 SDs).
+__device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cell, int64_t s, const uint32_t *w,
+                                                     uint32_t n, uint32_t rk)
+{
+    auto full_key = [&](uint32_t r) {
+        const uint4 k = draw4(seed, r >> 1, cell, s, 0u);
+        return (r & 1u) ? (((uint64_t)k.z << 32) | k.w) : (((uint64_t)k.x << 32) | k.y);
+    };
+    const uint64_t kk = full_key(rk);
+    uint32_t c = 0;
+    for (uint32_t m = 0; m < n; ++m) {
+        const uint32_t r = w[m] & 255u;
+        c += key_less(full_key(r), r, kk, rk) ? 1u : 0u;
+    }
+    return c;
+}
 
 template <int CAP, int WARPS, int STAGES>
 __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
@@ -426,10 +445,9 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
     unsigned char *mine = smem_raw + (size_t)warp * WarpSmem<CAP, STAGES>::per_warp;
     int64_t *st_xi = reinterpret_cast<int64_t *>(mine);               // [STAGES][CAP]
     double *st_v = reinterpret_cast<double *>(st_xi + STAGES * CAP);  // [STAGES][CAP]
-    uint64_t *s_key = reinterpret_cast<uint64_t *>(st_v + STAGES * CAP);
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_key + CAP);
-    uint16_t *s_rank = reinterpret_cast<uint16_t *>(s_hist + NB);
-    uint16_t *s_perm = s_rank + CAP;
+    uint32_t *s_word = reinterpret_cast<uint32_t *>(st_v + STAGES * CAP);
+    uint32_t *s_hist = s_word + CAP;
+    uint16_t *s_perm = reinterpret_cast<uint16_t *>(s_hist + NB);
     WQEntry *s_q = reinterpret_cast<WQEntry *>(s_perm + CAP);
     __shared__ uint64_t s_bar_all[WARPS][STAGES];
     __shared__ int4 s_meta_all[WARPS][STAGES];
@@ -522,29 +540,30 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             s_hist[lane + 32 * i] = 0u;
         __syncwarp();
 
-        // sort keys of live SDs and their bucket slots
-        uint64_t key[2 * RP];
+        // Sort words of live SDs and their bucket slots.  A word holds the
+        // top 24 bits of the SD's 64-bit key and its 8-bit rank, so words
+        // order as (key, rank) except between keys that share those 24 bits;
+        // such keys fall in one bucket and the fixup below orders them by
+        // their full keys.  Every lane draws all its Philox blocks first so
+        // that the independent chains interleave.
+        uint4 kw[RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r)
+            kw[r] = draw4(seed, (uint32_t)(lane + 32 * r), cell, s, 0u);
+        uint32_t word[2 * RP];
         uint32_t slot[2 * RP];
 #pragma unroll
         for (int r = 0; r < RP; ++r) {
             const int q = lane + 32 * r;
             slot[2 * r] = 0xFFFFFFFFu;
             slot[2 * r + 1] = 0xFFFFFFFFu;
-            key[2 * r] = 0;
-            key[2 * r + 1] = 0;
+            word[2 * r] = (kw[r].x & 0xFFFFFF00u) | (uint32_t)(2 * q);
+            word[2 * r + 1] = (kw[r].z & 0xFFFFFF00u) | (uint32_t)(2 * q + 1);
             if (2 * q < n) {
-                const bool la = xs[2 * q] > 0, lb = xs[2 * q + 1] > 0;
-                if (la | lb) {
-                    const uint4 w = draw4(seed, (uint32_t)q, cell, s, 0u);
-                    if (la) {
-                        key[2 * r] = ((uint64_t)w.x << 32) | w.y;
-                        slot[2 * r] = atomicAdd(&s_hist[key[2 * r] >> (64 - LB)], 1u);
-                    }
-                    if (lb) {
-                        key[2 * r + 1] = ((uint64_t)w.z << 32) | w.w;
-                        slot[2 * r + 1] = atomicAdd(&s_hist[key[2 * r + 1] >> (64 - LB)], 1u);
-                    }
-                }
+                if (xs[2 * q] > 0)
+                    slot[2 * r] = atomicAdd(&s_hist[word[2 * r] >> (32 - LB)], 1u);
+                if (xs[2 * q + 1] > 0)
+                    slot[2 * r + 1] = atomicAdd(&s_hist[word[2 * r + 1] >> (32 - LB)], 1u);
             }
         }
         __syncwarp();
@@ -574,27 +593,25 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
 
         if (n_c >= 2) {
 #pragma unroll
-            for (int r = 0; r < RP; ++r) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (slot[2 * r + h] != 0xFFFFFFFFu) {
-                        const uint32_t pos = s_hist[key[2 * r + h] >> (64 - LB)] + slot[2 * r + h];
-                        s_key[pos] = key[2 * r + h];
-                        s_rank[pos] = (uint16_t)(2 * (lane + 32 * r) + h);
-                    }
-                }
-            }
+            for (int i = 0; i < 2 * RP; ++i)
+                if (slot[i] != 0xFFFFFFFFu)
+                    s_word[s_hist[word[i] >> (32 - LB)] + slot[i]] = word[i];
             __syncwarp();
             for (uint32_t pos = lane; pos < n_c; pos += 32) {
-                const uint64_t kk = s_key[pos];
-                const uint32_t rk = s_rank[pos];
-                const uint32_t b = (uint32_t)(kk >> (64 - LB));
+                const uint32_t wv = s_word[pos];
+                const uint32_t b = wv >> (32 - LB);
                 const uint32_t lo = s_hist[b];
                 const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
                 uint32_t c = 0;
-                for (uint32_t m = lo; m < hi; ++m)
-                    c += key_less(s_key[m], s_rank[m], kk, rk) ? 1u : 0u;
-                s_perm[lo + c] = (uint16_t)rk;
+                bool tie = false;
+                for (uint32_t m = lo; m < hi; ++m) {
+                    const uint32_t wm = s_word[m];
+                    c += wm < wv ? 1u : 0u;
+                    tie |= ((wm ^ wv) < 256u) & (wm != wv);
+                }
+                if (tie)
+                    c = rank_in_bucket_full(seed, cell, s, s_word + lo, hi - lo, wv & 255u);
+                s_perm[lo + c] = (uint16_t)(wv & 255u);
             }
             __syncwarp();
 
@@ -608,29 +625,38 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             for (uint32_t q0 = 0; q0 < n_q; q0 += 32) { // warp-uniform trip count
                 const uint32_t q = q0 + lane;
                 const uint4 w = draw4(seed, q, cell, s, 1u);
+                uint32_t A[2], B[2];
+                int32_t gf[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t l = 2 * q + h;
-                    const bool valid = q < n_q && l < n_pairs;
-                    uint32_t a = 0, b = 0;
-                    int32_t gf = 0;
-                    const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
-                    if (valid) {
+                    A[h] = 0;
+                    B[h] = 0;
+                    gf[h] = 0;
+                    if (q < n_q && l < n_pairs) {
                         const uint32_t ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
-                        a = ab & 0xFFFFu;
-                        b = ab >> 16;
-                        int64_t xa = xs[a], xb = xs[b];
+                        uint32_t a = ab & 0xFFFFu, b = ab >> 16;
+                        int64_t xa = xs[a];
+                        const int64_t xb = xs[b];
                         if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
                             const uint32_t tmp = a;
                             a = b;
                             b = tmp;
                             xa = xb;
                         }
-                        gf = pair_gamma_filter(C, ratio_f, xa, vs_words[2 * a + 1], vs_words[2 * b + 1], wa);
+                        A[h] = a;
+                        B[h] = b;
+                        gf[h] = pair_gamma_filter(C, ratio_f, xa, vs_words[2 * a + 1], vs_words[2 * b + 1],
+                                                  h ? w.z : w.x);
                     }
-                    const bool und = gf != 0;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const bool und = gf[h] != 0;
                     const unsigned m = __ballot_sync(FULL, und);
                     if (m) {
+                        const uint32_t a = A[h], b = B[h];
+                        const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
                         const uint32_t base = s_qn;
                         const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
                         if (und) {
@@ -642,13 +668,13 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                                 E.wb = wb;
                                 E.n_c = n_c;
                                 E.inst = meta.w;
-                                E.gamma = gf;
+                                E.gamma = gf[h];
                                 s_q[idx] = E;
                             } else { // queue full: update here
                                 int64_t xa = xs[a], xb = xs[b];
                                 double va = vs[a], vb = vs[b];
-                                const int64_t g = gf > 0 ? cap_gamma(gf, xa, xb)
-                                                         : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                                const int64_t g = gf[h] > 0 ? cap_gamma(gf[h], xa, xb)
+                                                            : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
                                 if (g > 0) {
                                     const bool split = shima_update(g, xa, xb, va, vb);
                                     gxi[a] = xa;

@@ -230,6 +230,28 @@ def test_full_grid_two_steps(env):
     run.close()
 
 
+def test_sort_keys_sharing_their_top_bits(env):
+    """Cells of the full grid (seed 0, step 0) in which two keys share their
+    top 24 bits, order against their ranks and fall in different pairs
+    (golden/sort_word_ties.txt, from the oracle's keys).  dV = 1e-3 makes
+    p >> 1, so every pair collides and a wrong pairing shows in the state."""
+    import os
+
+    O, sdm, torch = env
+    path = os.path.join(os.path.dirname(__file__), "golden", "sort_word_ties.txt")
+    cells = sorted({int(line.split()[0]) for line in open(path) if not line.startswith("#")})
+    g = I.grid_geometric(seed=0)
+    keep = np.isin(g.cell, cells)
+    xi, v, cell = g.xi[keep], g.v[keep], g.cell[keep]
+    assert len(xi) == 256 * len(cells)
+    run = _gpu_run(sdm, "geometric", "fp64", xi, v, cell, g.n_cells, 1e-3, 0, 1)
+    gx, gv = run.attributes()
+    st = _oracle_run(O, "geometric", "fp64", xi, v, cell, g.n_cells, 1e-3, 0, 1)
+    _assert_same(gx, gv, st, "24-bit key ties")
+    assert int((gx != xi).sum()) > 0.9 * len(xi)
+    run.close()
+
+
 def test_device_inputs_and_outputs(env):
     O, sdm, torch = env
     g = I.grid_geometric(side=4, sd_per_cell=200, seed=8)

@@ -75,3 +75,33 @@ def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c):
     mean = tot / runs
     # gamma per pair is Bernoulli(p) with p <= 1/2 here: variance <= want
     assert abs(mean - want) < 5 * math.sqrt(want / runs)
+
+
+def _tie_fixture():
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "sort_word_ties.txt")
+    return [tuple(int(t) for t in line.split()) for line in open(path) if not line.startswith("#")]
+
+
+def test_keys_sharing_their_top_bits_are_ordered_by_the_full_key(oracle_lib):
+    """The cells listed in golden/sort_word_ties.txt hold two keys that agree
+    in their top 24 bits and order against their ranks; the permutation
+    orders them by the full 64-bit key, so the later rank comes first."""
+    import importlib.util
+    import os
+
+    O = oracle_lib
+    spec = importlib.util.spec_from_file_location(
+        "make_ties", os.path.join(os.path.dirname(__file__), "golden", "make_sort_word_ties.py"))
+    M = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(M)
+    rows = _tie_fixture()
+    assert len(rows) >= 5
+    for cell, p in rows:
+        assert p in M.tie_positions(cell)
+        perm = O.permutation(0, cell, 0, np.ones(256, np.int64))
+        a, b = int(perm[p]), int(perm[p + 1])
+        assert a > b
+        ka, kb = O.sort_key(0, a, cell, 0), O.sort_key(0, b, cell, 0)
+        assert ka >> 40 == kb >> 40 and ka < kb
