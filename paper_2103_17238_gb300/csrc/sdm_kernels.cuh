@@ -409,6 +409,54 @@ struct WarpSmem {
         (size_t)CAP * (16 * STAGES + 4 + 4 + 2) + sizeof(WQEntry) * (size_t)kWarpQueue;
 };
 
+__device__ __forceinline__ void cmp_swap(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = min(a, b);
+    b = max(a, b);
+    a = lo;
+}
+
+// Sorts E = 2, 4 or 8 words held in registers (Batcher's odd-even merge
+// networks: 1, 5 and 19 comparators).
+template <int E>
+__device__ __forceinline__ void sort_net(uint32_t (&v)[E])
+{
+    if constexpr (E == 2) {
+        cmp_swap(v[0], v[1]);
+    } else if constexpr (E == 4) {
+        cmp_swap(v[0], v[1]);
+        cmp_swap(v[2], v[3]);
+        cmp_swap(v[0], v[2]);
+        cmp_swap(v[1], v[3]);
+        cmp_swap(v[1], v[2]);
+    } else {
+        static_assert(E == 8, "sort_net: 2, 4 or 8 words");
+        cmp_swap(v[0], v[1]);
+        cmp_swap(v[2], v[3]);
+        cmp_swap(v[4], v[5]);
+        cmp_swap(v[6], v[7]);
+        cmp_swap(v[0], v[2]);
+        cmp_swap(v[1], v[3]);
+        cmp_swap(v[4], v[6]);
+        cmp_swap(v[5], v[7]);
+        cmp_swap(v[1], v[2]);
+        cmp_swap(v[5], v[6]);
+        cmp_swap(v[0], v[4]);
+        cmp_swap(v[1], v[5]);
+        cmp_swap(v[2], v[6]);
+        cmp_swap(v[3], v[7]);
+        cmp_swap(v[2], v[4]);
+        cmp_swap(v[3], v[5]);
+        cmp_swap(v[1], v[2]);
+        cmp_swap(v[3], v[4]);
+        cmp_swap(v[5], v[6]);
+    }
+}
+
+// Swap rounds of the lane-block sort before the per-element fixup takes
+// over (one to three rounds suffice for bucket-ordered random words).
+constexpr int kMaxSwapRounds = 32;
+
 // Position, among the n words of one bucket, of the SD of rank rk in full
 // (key, rank) order; the keys are drawn again.  Taken only by buckets in
 // which two keys share their top 24 bits (about one cell in 500 at 256 SDs).
@@ -597,21 +645,88 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                 if (slot[i] != 0xFFFFFFFFu)
                     s_word[s_hist[word[i] >> (32 - LB)] + slot[i]] = word[i];
             __syncwarp();
-            for (uint32_t pos = lane; pos < n_c; pos += 32) {
-                const uint32_t wv = s_word[pos];
-                const uint32_t b = wv >> (32 - LB);
-                const uint32_t lo = s_hist[b];
-                const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
-                uint32_t c = 0;
-                bool tie = false;
-                for (uint32_t m = lo; m < hi; ++m) {
-                    const uint32_t wm = s_word[m];
-                    c += wm < wv ? 1u : 0u;
-                    tie |= ((wm ^ wv) < 256u) & (wm != wv);
+            // Lane L sorts positions E L .. E L + E - 1 of the bucket-ordered
+            // words in registers (positions >= n_c hold 0xFFFFFFFF).  Words
+            // can then be out of order only inside buckets that straddle a
+            // lane boundary; neighbouring lanes swap inverted boundary words
+            // and sort again until no boundary is inverted (every swap
+            // removes an inversion).  Equal 24-bit prefixes end up adjacent;
+            // cells holding one take the per-element fixup with full keys.
+            constexpr int E = CAP / 32;
+            uint32_t v[E];
+            if constexpr (E == 2) {
+                const uint2 t = reinterpret_cast<const uint2 *>(s_word)[lane];
+                v[0] = t.x;
+                v[1] = t.y;
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; i += 4) {
+                    const uint4 t = reinterpret_cast<const uint4 *>(s_word + E * lane + i)[0];
+                    v[i] = t.x;
+                    v[i + 1] = t.y;
+                    v[i + 2] = t.z;
+                    v[i + 3] = t.w;
                 }
-                if (tie)
-                    c = rank_in_bucket_full(seed, cell, s, s_word + lo, hi - lo, wv & 255u);
-                s_perm[lo + c] = (uint16_t)(wv & 255u);
+            }
+#pragma unroll
+            for (int i = 0; i < E; ++i)
+                if ((uint32_t)(E * lane + i) >= n_c)
+                    v[i] = 0xFFFFFFFFu;
+            sort_net<E>(v);
+            bool fast = true;
+            for (int round = 0;; ++round) {
+                const uint32_t prev_last = __shfl_up_sync(FULL, v[E - 1], 1);
+                const uint32_t next_first = __shfl_down_sync(FULL, v[0], 1);
+                const bool lo_inv = lane > 0 && prev_last > v[0];
+                const bool hi_inv = lane < 31 && v[E - 1] > next_first;
+                if (!__any_sync(FULL, lo_inv || hi_inv))
+                    break;
+                if (round == kMaxSwapRounds) {
+                    fast = false;
+                    break;
+                }
+                if (lo_inv)
+                    v[0] = prev_last;
+                if (hi_inv)
+                    v[E - 1] = next_first;
+                sort_net<E>(v);
+            }
+            bool prefix_tie = false;
+#pragma unroll
+            for (int i = 0; i + 1 < E; ++i)
+                prefix_tie |= ((v[i] ^ v[i + 1]) < 256u) & (v[i] != v[i + 1]);
+            const uint32_t nf = __shfl_down_sync(FULL, v[0], 1);
+            if (lane < 31)
+                prefix_tie |= ((v[E - 1] ^ nf) < 256u) & (v[E - 1] != nf);
+            if (fast && !__any_sync(FULL, prefix_tie)) {
+                uint32_t pk[E / 2];
+#pragma unroll
+                for (int i = 0; i < E / 2; ++i)
+                    pk[i] = (v[2 * i] & 255u) | ((v[2 * i + 1] & 255u) << 16);
+                if constexpr (E == 2) {
+                    reinterpret_cast<uint32_t *>(s_perm)[lane] = pk[0];
+                } else if constexpr (E == 4) {
+                    reinterpret_cast<uint2 *>(s_perm)[lane] = make_uint2(pk[0], pk[1]);
+                } else {
+                    reinterpret_cast<uint4 *>(s_perm)[lane] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+            } else {
+                for (uint32_t pos = lane; pos < n_c; pos += 32) {
+                    const uint32_t wv = s_word[pos];
+                    const uint32_t b = wv >> (32 - LB);
+                    const uint32_t lo = s_hist[b];
+                    const uint32_t hi = (b + 1 < (uint32_t)NB) ? s_hist[b + 1] : n_c;
+                    uint32_t c = 0;
+                    bool tie = false;
+                    for (uint32_t m = lo; m < hi; ++m) {
+                        const uint32_t wm = s_word[m];
+                        c += wm < wv ? 1u : 0u;
+                        tie |= ((wm ^ wv) < 256u) & (wm != wv);
+                    }
+                    if (tie)
+                        c = rank_in_bucket_full(seed, cell, s, s_word + lo, hi - lo, wv & 255u);
+                    s_perm[lo + c] = (uint16_t)(wv & 255u);
+                }
             }
             __syncwarp();
 
