@@ -345,14 +345,16 @@ __device__ __forceinline__ float xi2f(int64_t x)
 // where the filter's radius could fall on the other side of it.
 __device__ __forceinline__ float vt_guarded(const PairConsts &C, float r, bool &ok)
 {
-    if (r < C.r1_lo)
-        return C.k1f * (r * r);
-    if (r < C.r2_lo) {
-        ok &= r > C.r1_hi;
-        return C.k2f * r;
+    // regimes 1 and 2 by a select (no divergence); regime 3 (the largest
+    // drops, rare) by a branch
+    const bool reg1 = r < C.r1_lo;
+    float t = reg1 ? C.k1f * (r * r) : C.k2f * r;
+    ok &= reg1 | (r > C.r1_hi);
+    if (r >= C.r2_lo) {
+        ok &= r > C.r2_hi;
+        t = C.k3f * sqrtf(r);
     }
-    ok &= r > C.r2_hi;
-    return C.k3f * sqrtf(r);
+    return t;
 }
 
 // The collision count ceil(p - u) of a pair (xi_j >= xi_k > 0) when the
@@ -420,8 +422,13 @@ __device__ __forceinline__ int64_t cap_gamma(int32_t g, int64_t xi_j, int64_t xi
 {
     if (g == 1)
         return 1; // xi_j >= xi_k
-    const int64_t q = xi_j / xi_k;
-    return (int64_t)g < q ? (int64_t)g : q;
+    // g xi_k <= xi_j (no overflow: the 128-bit product's high word is zero)
+    // means floor(xi_j / xi_k) >= g; only the capped case divides
+    const uint64_t lo = (uint64_t)g * (uint64_t)xi_k;
+    const uint64_t hi = __umul64hi((uint64_t)g, (uint64_t)xi_k);
+    if (hi == 0 && lo <= (uint64_t)xi_j)
+        return g;
+    return xi_j / xi_k;
 }
 
 // ------------------------------------------------------------ exact gamma

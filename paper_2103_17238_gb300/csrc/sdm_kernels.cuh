@@ -400,6 +400,8 @@ struct WQEntry {
     int32_t gamma;           // certain collision count (>= 1), or -1: evaluate exactly
 };
 
+// The warp kernel queues only the pairs its filter cannot decide (certain
+// collisions are updated in place), so the queue holds few entries.
 constexpr int kWarpQueue = 96;
 
 template <int CAP, int STAGES>
@@ -767,10 +769,21 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const bool und = gf[h] != 0;
+                    const uint32_t a = A[h], b = B[h];
+                    if (gf[h] > 0) { // a certain collision: update from the staged state now
+                        int64_t xa = xs[a], xb = xs[b];
+                        double va = vs[a], vb = vs[b];
+                        const bool split = shima_update(cap_gamma(gf[h], xa, xb), xa, xb, va, vb);
+                        gxi[a] = xa;
+                        gxi[b] = xb;
+                        gv[b] = vb;
+                        if (split)
+                            gv[a] = va;
+                    }
+                    // pairs the filter could not decide wait for the exact evaluation
+                    const bool und = gf[h] < 0;
                     const unsigned m = __ballot_sync(FULL, und);
                     if (m) {
-                        const uint32_t a = A[h], b = B[h];
                         const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
                         const uint32_t base = s_qn;
                         const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
@@ -783,13 +796,12 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                                 E.wb = wb;
                                 E.n_c = n_c;
                                 E.inst = meta.w;
-                                E.gamma = gf[h];
+                                E.gamma = -1;
                                 s_q[idx] = E;
-                            } else { // queue full: update here
+                            } else { // queue full: evaluate here
                                 int64_t xa = xs[a], xb = xs[b];
                                 double va = vs[a], vb = vs[b];
-                                const int64_t g = gf[h] > 0 ? cap_gamma(gf[h], xa, xb)
-                                                            : pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                                const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
                                 if (g > 0) {
                                     const bool split = shima_update(g, xa, xb, va, vb);
                                     gxi[a] = xa;
