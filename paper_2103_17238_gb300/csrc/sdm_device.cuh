@@ -335,10 +335,29 @@ __device__ __forceinline__ float hi2f(uint32_t hi, bool &in_range)
     return __uint_as_float((hi << 3) - (896u << 23));
 }
 
-// Binary32 image of a multiplicity, relative error < 2^-23.
+// Binary32 image of a multiplicity x >= 1 truncated to 24 bits (relative
+// error < 2^-23), built on the integer pipe: 64-bit conversions would run on
+// the scarce binary64 pipe.
 __device__ __forceinline__ float xi2f(int64_t x)
 {
-    return ((uint64_t)x >> 32) == 0 ? __uint2float_rz((uint32_t)x) : __ll2float_rz(x);
+    const uint64_t u = (uint64_t)x;
+    const uint32_t lz = (uint32_t)__clzll((long long)u); // < 64 for x >= 1
+    const uint32_t top = (uint32_t)((u << lz) >> 40);    // leading 24 bits, bit 23 set
+    return __uint_as_float(((190u - lz) << 23) + (top & 0x7FFFFFu));
+}
+
+// The binary64 value of a multiplicity 0 <= x < 2^53 (exact) built on the
+// integer pipe; larger x by the conversion instruction (round to nearest).
+__device__ __forceinline__ double xi2d(int64_t x)
+{
+    const uint64_t u = (uint64_t)x;
+    if (u >> 53)
+        return __ll2double_rn(x);
+    if (u == 0)
+        return 0.0;
+    const uint32_t lz = (uint32_t)__clzll((long long)u);           // 11 .. 63
+    const uint64_t mant = (u << (lz - 11)) & 0x000FFFFFFFFFFFFFull; // 52 bits below the leading one
+    return __longlong_as_double((long long)(((uint64_t)(1086u - lz) << 52) | mant));
 }
 
 // Fall speed for the filter; clears ok within 2^-14 of a regime boundary,
@@ -466,7 +485,9 @@ __device__ __forceinline__ int64_t pair_gamma_exact(const InstDev *P, uint32_t n
 __device__ __forceinline__ bool shima_update(int64_t gamma, int64_t &xi_j, int64_t &xi_k, double &vj, double &vk)
 {
     // (double)1 * v_j is v_j exactly: one binary64 add for the common gamma = 1
-    const double t = gamma == 1 ? vj : __dmul_rn(__ll2double_rn(gamma), vj);
+    double t = vj;
+    if (gamma != 1)
+        t = __dmul_rn(__ll2double_rn(gamma), vj);
     const double vnew = __dadd_rn(vk, t);
     const int64_t rem = xi_j - gamma * xi_k;
     if (rem > 0) {

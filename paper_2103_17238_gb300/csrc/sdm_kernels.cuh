@@ -10,7 +10,8 @@
 //      histogram pass over chunks, a per-cell scan, a scatter of (key, rank)
 //      into bucket order in global scratch, a per-bucket shared-memory sort
 //      on the next key bits, and a pair pass gathering from the state.
-//  spectrum_kernel             dv/dlnr accumulation per cell or in total.
+//  spectrum kernels            dv/dlnr accumulation per cell, or in total
+//                              without atomics (fixed summation order).
 //  layout / gather kernels     set_attributes and get_attributes.
 #pragma once
 
@@ -1116,10 +1117,79 @@ __global__ void advance_steps_kernel(InstDev *const *insts, int32_t n_inst, int6
 constexpr int kSpecNT = 256;
 constexpr int kMaxEdges = 1024;
 
-// One CTA per cell: live SDs binned by radius, sum(xi v) per bin.  The bin
-// of every SD is the one the exact cube root gives: a binary32 radius
-// (relative error below 2^-18.8) decides it when it lies more than 2^-14
-// from every bin edge, else the exact binary64 radius and search do.
+// Bin of a live SD of volume v among the edges (-1: outside [e_0, e_N)).
+// The binary32 radius decides when it lies clear (2^-14 relative) of every
+// bin edge, else the exact binary64 radius and search do.
+__device__ __forceinline__ int spectrum_bin(double v, const double *s_edges, const float *s_lo, const float *s_hi,
+                                            int n_edges)
+{
+    const int nb = n_edges - 1;
+    bool in_range;
+    const float rf = cbrt_filter(hi2f((uint32_t)__double2hiint(v), in_range) * kVolToR3F);
+    // largest lo with lower(edge[lo]) <= rf
+    int lo = -1, hi = n_edges;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_lo[mid] <= rf)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const bool clear_below = lo >= 0 && rf > s_hi[lo];
+    const bool clear_above = lo + 1 >= n_edges || rf < s_lo[lo + 1];
+    if (in_range && (lo < 0 || clear_below) && clear_above)
+        return (lo < 0 || lo >= nb) ? -1 : lo;
+    const double r = radius_exact(v);
+    if (r < s_edges[0] || !(r < s_edges[n_edges - 1]))
+        return -1;
+    int a = 0, z = n_edges - 1;
+    while (z - a > 1) {
+        const int mid = (a + z) >> 1;
+        if (s_edges[mid] <= r)
+            a = mid;
+        else
+            z = mid;
+    }
+    return a;
+}
+
+// The same with a fixed-step search over at most MAXE - 1 edges (unrolled,
+// so that the searches of neighbouring SDs interleave).
+template <int MAXE>
+__device__ __forceinline__ int spectrum_bin_fixed(double v, const double *s_edges, const float *s_lo,
+                                                  const float *s_hi, int n_edges)
+{
+    const int nb = n_edges - 1;
+    bool in_range;
+    const float rf = cbrt_filter(hi2f((uint32_t)__double2hiint(v), in_range) * kVolToR3F);
+    int lo = -1; // largest lo with lower(edge[lo]) <= rf
+#pragma unroll
+    for (int step = MAXE / 2; step > 0; step >>= 1) {
+        const int mid = lo + step;
+        if (mid < n_edges && s_lo[mid] <= rf)
+            lo = mid;
+    }
+    const bool clear_below = lo >= 0 && rf > s_hi[lo];
+    const bool clear_above = lo + 1 >= n_edges || rf < s_lo[lo + 1];
+    if (in_range && (lo < 0 || clear_below) && clear_above)
+        return (lo < 0 || lo >= nb) ? -1 : lo;
+    return spectrum_bin(v, s_edges, s_lo, s_hi, n_edges);
+}
+
+// Edges into shared memory with their binary32 images widened by 2^-14.
+__device__ __forceinline__ void spectrum_edges_to_smem(const double *edges, int n_edges, double *s_edges, float *s_lo,
+                                                       float *s_hi)
+{
+    for (int i = threadIdx.x; i < n_edges; i += blockDim.x) {
+        const double e = edges[i];
+        s_edges[i] = e;
+        const float ef = __double2float_rn(e);
+        s_lo[i] = ef * (1.0f - 0x1p-14f);
+        s_hi[i] = ef * (1.0f + 0x1p-14f);
+    }
+}
+
+// dv/dlnr accumulation, one block per cell: sum of xi v per bin of live SDs.
 // per_cell: acc[cell * nb + b]; otherwise atomically into acc[b].
 __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__restrict__ P, const double *__restrict__ edges,
                                                            int32_t n_edges, int32_t per_cell, double *__restrict__ acc)
@@ -1129,13 +1199,7 @@ __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__rest
     __shared__ double s_acc[kMaxEdges];
     const int cell = blockIdx.x;
     const int nb = n_edges - 1;
-    for (int i = threadIdx.x; i < n_edges; i += kSpecNT) {
-        const double e = edges[i];
-        s_edges[i] = e;
-        const float ef = __double2float_rn(e);
-        s_lo[i] = ef * (1.0f - 0x1p-14f);
-        s_hi[i] = ef * (1.0f + 0x1p-14f);
-    }
+    spectrum_edges_to_smem(edges, n_edges, s_edges, s_lo, s_hi);
     for (int i = threadIdx.x; i < nb; i += kSpecNT)
         s_acc[i] = 0.0;
     __syncthreads();
@@ -1148,38 +1212,9 @@ __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__rest
         if (x <= 0)
             continue;
         const double v = gv[i];
-        bool in_range;
-        const float rf = cbrt_filter(hi2f((uint32_t)__double2hiint(v), in_range) * kVolToR3F);
-        // largest lo with lower(edge[lo]) <= rf
-        int lo = -1, hi = n_edges;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_lo[mid] <= rf)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        int bin;
-        const bool clear_below = lo >= 0 && rf > s_hi[lo];
-        const bool clear_above = lo + 1 >= n_edges || rf < s_lo[lo + 1];
-        if (in_range && (lo < 0 || clear_below) && clear_above) {
-            bin = (lo < 0 || lo >= nb) ? -1 : lo; // outside [e_0, e_N): dropped
-        } else {
-            const double r = radius_exact(v);
-            if (r < s_edges[0] || !(r < s_edges[n_edges - 1]))
-                continue;
-            int a = 0, z = n_edges - 1;
-            while (z - a > 1) {
-                const int mid = (a + z) >> 1;
-                if (s_edges[mid] <= r)
-                    a = mid;
-                else
-                    z = mid;
-            }
-            bin = a;
-        }
+        const int bin = spectrum_bin(v, s_edges, s_lo, s_hi, n_edges);
         if (bin >= 0)
-            atomicAdd(&s_acc[bin], __dmul_rn(__ll2double_rn(x), v));
+            atomicAdd(&s_acc[bin], __dmul_rn(xi2d(x), v));
     }
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += kSpecNT) {
@@ -1190,37 +1225,131 @@ __global__ void __launch_bounds__(kSpecNT) spectrum_kernel(const InstDev *__rest
     }
 }
 
-// out[i] = acc[i] / vol / (ln e[b+1] - ln e[b])
-__global__ void spectrum_finalize_kernel(const double *__restrict__ acc, const double *__restrict__ edges,
-                                         int32_t n_edges, int64_t n_out, double vol, double *__restrict__ out)
+// Total spectrum without atomics: a grid-stride pass over every storage slot
+// (padding and dead SDs hold xi = 0); each thread adds into its own column
+// of a bins x threads shared array, then each block sums its columns in a
+// fixed order into partial[bin][block].  Results repeat bit for bit.
+constexpr int kSpecTotNT = 128;
+constexpr int kSpecTotMaxBins = 32;
+
+__global__ void __launch_bounds__(kSpecTotNT) spectrum_total_kernel(const InstDev *__restrict__ P, int64_t n_slots,
+                                                                    const double *__restrict__ edges, int32_t n_edges,
+                                                                    double *__restrict__ partial)
+{
+    __shared__ double s_col[kSpecTotMaxBins * kSpecTotNT];
+    __shared__ double s_edges[kSpecTotMaxBins + 1];
+    __shared__ float s_lo[kSpecTotMaxBins + 1], s_hi[kSpecTotMaxBins + 1];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nb = n_edges - 1;
+    spectrum_edges_to_smem(edges, n_edges, s_edges, s_lo, s_hi);
+    for (int b = 0; b < nb; ++b)
+        s_col[b * kSpecTotNT + t] = 0.0;
+    __syncthreads();
+    const int64_t *__restrict__ gxi = P->xi;
+    const double *__restrict__ gv = P->v;
+    // four slots per iteration, all loads issued before any is used
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * kSpecTotNT;
+    for (int64_t i0 = (int64_t)blockIdx.x * kSpecTotNT + t; i0 < n_slots; i0 += U * stride) {
+        int64_t x[U];
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            x[u] = i < n_slots ? gxi[i] : 0;
+            v[u] = i < n_slots ? gv[i] : 1.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (x[u] <= 0)
+                continue;
+            const int bin = spectrum_bin_fixed<2 * kSpecTotMaxBins>(v[u], s_edges, s_lo, s_hi, n_edges);
+            if (bin >= 0) // xi v added with one rounding
+                s_col[bin * kSpecTotNT + t] = __fma_rn(xi2d(x[u]), v[u], s_col[bin * kSpecTotNT + t]);
+        }
+    }
+    __syncthreads();
+    for (int b = warp; b < nb; b += kSpecTotNT / 32) {
+        double sum = 0.0;
+        for (int j = lane; j < kSpecTotNT; j += 32)
+            sum = __dadd_rn(sum, s_col[b * kSpecTotNT + j]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+            sum = __dadd_rn(sum, __shfl_down_sync(0xFFFFFFFFu, sum, d));
+        if (lane == 0)
+            partial[(int64_t)b * gridDim.x + blockIdx.x] = sum;
+    }
+}
+
+// out[b] = (sum over blocks of partial[b][block], fixed order) / vol / dln[b],
+// dln[b] = ln e[b+1] - ln e[b] (from the host); one warp (block) per bin.
+__global__ void spectrum_total_finalize_kernel(const double *__restrict__ partial, int32_t n_blocks,
+                                               const double *__restrict__ dln, int32_t nb, double vol,
+                                               double *__restrict__ out)
+{
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb)
+        return;
+    double sum = 0.0;
+    for (int j = lane; j < n_blocks; j += 32)
+        sum = __dadd_rn(sum, partial[(int64_t)b * n_blocks + j]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        sum = __dadd_rn(sum, __shfl_down_sync(0xFFFFFFFFu, sum, d));
+    if (lane == 0)
+        out[b] = sum / vol / dln[b];
+}
+
+// out[i] = acc[i] / vol / dln[i mod nb]
+__global__ void spectrum_finalize_kernel(const double *__restrict__ acc, const double *__restrict__ dln, int32_t nb,
+                                         int64_t n_out, double vol, double *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_out)
         return;
-    const int nb = n_edges - 1;
-    const int b = (int)(i % nb);
-    out[i] = acc[i] / vol / (log(edges[b + 1]) - log(edges[b]));
+    out[i] = acc[i] / vol / dln[i % nb];
 }
 
 // --------------------------------------------------------------- layout
 // Validation and per-cell counts of set_attributes.  flags bit 0: an
 // invalid attribute (first bad SD index in *bad); bit 1: cells not sorted.
+// Each warp takes 32 consecutive SDs at a time and adds one count per run of
+// equal cell ids (one or two atomics per warp for cell-sorted input).
 __global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
                                       const int32_t *__restrict__ cell, int32_t n_cells, uint32_t *__restrict__ counts,
                                       uint32_t *__restrict__ flags, unsigned long long *__restrict__ bad)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sd; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = cell[i];
-        const double vi = v[i];
-        const bool ok = xi[i] >= 0 && vi >= 1e-30 && vi <= 1e30 && c >= 0 && c < n_cells;
-        if (!ok) {
-            atomicOr(flags, 1u);
-            atomicMin(bad, (unsigned long long)i);
-            continue;
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_sd; base += wstride) {
+        const int64_t i = base + lane;
+        const bool in = i < n_sd;
+        const int32_t craw = in ? cell[i] : INT32_MAX;
+        int32_t c = -1; // counted cell, -1: none
+        if (in) {
+            const double vi = v[i];
+            if (xi[i] >= 0 && vi >= 1e-30 && vi <= 1e30 && craw >= 0 && craw < n_cells) {
+                c = craw;
+            } else {
+                atomicOr(flags, 1u);
+                atomicMin(bad, (unsigned long long)i);
+            }
         }
-        atomicAdd(&counts[c], 1u);
-        if (i > 0 && cell[i - 1] > c)
+        int32_t prev = __shfl_up_sync(FULL, craw, 1);
+        if (lane == 0)
+            prev = (in && i > 0) ? cell[i - 1] : INT32_MIN;
+        if (__any_sync(FULL, in && prev > craw) && lane == 0)
             atomicOr(flags, 2u);
+        const int32_t next = __shfl_down_sync(FULL, c, 1);
+        const bool end = lane == 31 || next != c;
+        const unsigned ends = __ballot_sync(FULL, end);
+        if (end && c >= 0) {
+            const unsigned below = ends & ((1u << lane) - 1u);
+            const int start = below ? 32 - __clz(below) : 0;
+            atomicAdd(&counts[c], (uint32_t)(lane - start + 1));
+        }
     }
 }
 
@@ -1245,14 +1374,17 @@ __global__ void scatter_kernel(int64_t n_sd, const int64_t *__restrict__ xi, con
     }
 }
 
-// Padding slots: dead, with a harmless positive volume.
-__global__ void fill_padding_kernel(int64_t n_slots, int64_t *__restrict__ sxi, double *__restrict__ sv,
-                                    int32_t *__restrict__ id_of_slot)
+// Padding slots (the one slot after an odd cell): dead, with a harmless
+// positive volume.
+__global__ void fill_padding_kernel(int32_t n_cells, const int32_t *__restrict__ poff, const int32_t *__restrict__ uoff,
+                                    int64_t *__restrict__ sxi, double *__restrict__ sv, int32_t *__restrict__ id_of_slot)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += (int64_t)gridDim.x * blockDim.x) {
-        sxi[i] = 0;
-        sv[i] = 1.0;
-        id_of_slot[i] = -1;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        for (int32_t p = poff[c] + (uoff[c + 1] - uoff[c]); p < poff[c + 1]; ++p) {
+            sxi[p] = 0;
+            sv[p] = 1.0;
+            id_of_slot[p] = -1;
+        }
     }
 }
 

@@ -80,6 +80,7 @@ struct Plan {
     int max_big_lb = 0;
     std::vector<Buf> bufs;
     int64_t bytes = 0;
+    sdm_tuning tuning{}; // the launch tuning the plan was built with
 };
 
 } // namespace
@@ -232,8 +233,16 @@ Variant g_variants[] = {
 };
 constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 
+int g_spec_grid = 1; // blocks of the total-spectrum kernel (resident blocks x SMs)
+
 std::mutex g_tuning_mutex;
 sdm_tuning g_tuning = {4096, 256, 2, 0};
+
+bool same_tuning(const sdm_tuning &a, const sdm_tuning &b)
+{
+    return a.smem_max_sd == b.smem_max_sd && a.warp_cell_max == b.warp_cell_max &&
+           a.warps_per_block == b.warps_per_block;
+}
 
 sdm_tuning current_tuning()
 {
@@ -291,6 +300,11 @@ cudaError_t configure_kernels_once()
     }
         SDM_BLOCK_VARIANTS(X)
 #undef X
+        int spec_per_sm = 0;
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spec_per_sm, spectrum_total_kernel, kSpecTotNT, 0)) !=
+            cudaSuccess)
+            e = r;
+        g_spec_grid = std::max(1, spec_per_sm) * sms;
         const int hb = (int)big_hist_smem(kBigMaxLB);
         if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
@@ -331,6 +345,7 @@ sdm_status build_plan(sdm_batch *b)
     std::vector<InstDev *> insts(n_inst);
     int64_t hist_total = 0, sd_total = 0, bkt_total = 0;
     const sdm_tuning tun = current_tuning();
+    pl.tuning = tun;
     for (int k = 0; k < kNumClass; ++k)
         pl.variant[k] = variant_for(kClassCap[k], tun);
     for (int i = 0; i < n_inst; ++i) {
@@ -820,25 +835,34 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     CTX_CUDA(ctx, cudaMemcpyAsync(d_uoff, uoff.data(), sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
     if (d_pos)
         CTX_CUDA(ctx, cudaMemcpyAsync(d_pos, pos.data(), b_c, cudaMemcpyHostToDevice, s));
-    fill_padding_kernel<<<1216, 256, 0, s>>>(ps, ctx->d_xi, ctx->d_v, ctx->d_id_of_slot);
-    scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
-                                        ctx->d_id_of_slot);
-    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff.data(), sizeof(int32_t) * (n_cells + 1),
-                                  cudaMemcpyHostToDevice, s));
+    // a context's own launch plan depends only on the padded layout and the
+    // launch tuning: kept when both are unchanged
+    const bool keep_plan = ctx->self_batch && ctx->h_cell_off == poff &&
+                           same_tuning(ctx->self_batch->plan.tuning, current_tuning());
     ctx->n_sd = n_sd;
     ctx->n_slots = ps;
     ctx->largest_cell = largest;
     ctx->h_cell_off = poff;
     ctx->dev_base = ctx->step;
     InstDev inst = make_inst(ctx);
+    // Copies from pageable memory wait for the stream's earlier work, so the
+    // small ones (offsets, the record) go before the layout kernels; their
+    // sources are staged before the copies return, the caller's arrays were
+    // read before the validation sync, and the scratch is released in
+    // stream order: nothing waits for the kernels below.
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff.data(), sizeof(int32_t) * (n_cells + 1),
+                                  cudaMemcpyHostToDevice, s));
     CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
+    fill_padding_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(n_cells, d_poff, d_uoff, ctx->d_xi, ctx->d_v,
+                                                               ctx->d_id_of_slot);
+    scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
+                                        ctx->d_id_of_slot);
     CTX_CUDA(ctx, cudaGetLastError());
-    CTX_CUDA(ctx, cudaStreamSynchronize(s)); // host vectors above go out of scope
     mem.put(aux, b_aux);
     mem.put(meta, b_counts);
     mem.put(stage, b_stage);
     ctx->has_attributes = true;
-    if (ctx->self_batch) {
+    if (ctx->self_batch && !keep_plan) {
         batch_release(ctx->self_batch);
         delete ctx->self_batch;
         ctx->self_batch = nullptr;
@@ -891,19 +915,34 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     const int32_t nb = n_edges - 1;
     const int64_t n_out = per_cell ? (int64_t)ctx->cfg.n_cells * nb : nb;
     cudaStream_t s = ctx->stream;
-    const size_t b_edges = sizeof(double) * n_edges, b_acc = sizeof(double) * n_out;
-    const size_t b_tmp = b_edges + 2 * b_acc;
+    CTX_CUDA(ctx, configure_kernels_once());
+    // the total over all cells with few bins: the atomic-free kernel
+    const bool total = !per_cell && nb <= kSpecTotMaxBins;
+    const int grid = g_spec_grid;
+    // edges, then dln[b] = ln e[b+1] - ln e[b] (host logarithms), in one copy
+    std::vector<double> host_e(r_edges, r_edges + n_edges);
+    for (int32_t b = 0; b < nb; ++b)
+        host_e.push_back(std::log(r_edges[b + 1]) - std::log(r_edges[b]));
+    const size_t b_edges = sizeof(double) * host_e.size(), b_acc = sizeof(double) * n_out;
+    const size_t b_part = total ? sizeof(double) * (size_t)grid * nb : b_acc;
+    const size_t b_tmp = b_edges + b_part + b_acc;
     char *tmp = (char *)ctx->mem.get(b_tmp);
     if (!tmp)
         return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
     double *d_edges = (double *)tmp;
+    const double *d_dln = d_edges + n_edges;
     double *d_acc = (double *)(tmp + b_edges);
-    double *d_out = out_on_device ? out : (double *)(tmp + b_edges + b_acc);
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, r_edges, b_edges, cudaMemcpyHostToDevice, s));
-    CTX_CUDA(ctx, cudaMemsetAsync(d_acc, 0, b_acc, s));
-    spectrum_kernel<<<ctx->cfg.n_cells, kSpecNT, 0, s>>>(ctx->d_inst, d_edges, n_edges, per_cell ? 1 : 0, d_acc);
+    double *d_out = out_on_device ? out : (double *)(tmp + b_edges + b_part);
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, host_e.data(), b_edges, cudaMemcpyHostToDevice, s));
     const double vol = per_cell ? ctx->cfg.dv : ctx->cfg.dv * (double)ctx->cfg.n_cells;
-    spectrum_finalize_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(d_acc, d_edges, n_edges, n_out, vol, d_out);
+    if (total) {
+        spectrum_total_kernel<<<grid, kSpecTotNT, 0, s>>>(ctx->d_inst, ctx->n_slots, d_edges, n_edges, d_acc);
+        spectrum_total_finalize_kernel<<<nb, 32, 0, s>>>(d_acc, grid, d_dln, nb, vol, d_out);
+    } else {
+        CTX_CUDA(ctx, cudaMemsetAsync(d_acc, 0, b_acc, s));
+        spectrum_kernel<<<ctx->cfg.n_cells, kSpecNT, 0, s>>>(ctx->d_inst, d_edges, n_edges, per_cell ? 1 : 0, d_acc);
+        spectrum_finalize_kernel<<<(unsigned)((n_out + 255) / 256), 256, 0, s>>>(d_acc, d_dln, nb, n_out, vol, d_out);
+    }
     CTX_CUDA(ctx, cudaGetLastError());
     if (!out_on_device) {
         CTX_CUDA(ctx, cudaMemcpyAsync(out, d_out, b_acc, cudaMemcpyDeviceToHost, s));

@@ -191,6 +191,15 @@ def test_spectrum_bin_edges(env):
     want = O.spectrum(P, st, e, per_cell=True)
     assert np.allclose(got, want, rtol=1e-12, atol=0)
     assert np.array_equal(got > 0, want > 0)
+    # the total over cells (up to 32 bins: the atomic-free kernel, whose
+    # fixed summation order repeats bit for bit), and with 63 bins
+    got_t = run.spectrum(e)
+    want_t = O.spectrum(P, st, e)
+    assert np.allclose(got_t, want_t, rtol=1e-12, atol=0)
+    assert np.array_equal(got_t > 0, want_t > 0)
+    assert np.array_equal(run.spectrum(e), got_t)
+    e64 = np.logspace(np.log10(10.0e-6), np.log10(5.0e-3), 64)
+    assert np.allclose(run.spectrum(e64), O.spectrum(P, st, e64), rtol=1e-12, atol=0)
     run.close()
 
 
@@ -284,6 +293,30 @@ def test_resume_bit_exact(env):
     x2, v2 = b.attributes()
     assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
     for r in (straight, a, b):
+        r.close()
+
+
+def test_new_attributes_keep_or_rebuild_the_plan(env):
+    """set_attributes on a stepped context: a new state with the same cell
+    layout (the launch plan is kept) and then one with another layout (the
+    plan is rebuilt) continue exactly like fresh contexts started at those
+    steps, and like the oracle."""
+    O, sdm, torch = env
+    g = I.grid_geometric(side=4, sd_per_cell=256, seed=3)
+    xi2, v2 = g.xi // 3 + 1, g.v * 1.7
+    rng = np.random.default_rng(5)
+    xi3, v3, c3 = _ragged_state(rng, RAGGED[:16], 1e3)
+    run = _gpu_run(sdm, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 3, 4)
+    run.set_attributes(xi2, v2, g.cell).step(5)
+    ref = _gpu_run(sdm, "geometric", "fp64", xi2, v2, g.cell, g.n_cells, g.dv, 3, 5, step0=4)
+    for a, b in zip(run.attributes(), ref.attributes()):
+        assert np.array_equal(a, b)
+    run.set_attributes(xi3, v3, c3).step(3)
+    gx, gv = run.attributes()
+    st = _oracle_run(O, "geometric", "fp64", xi3, v3, c3, g.n_cells, g.dv, 3, 3, s0=9)
+    _assert_same(gx, gv, st, "new layout after 9 steps")
+    assert run.info().step == 12
+    for r in (run, ref):
         r.close()
 
 
