@@ -139,6 +139,17 @@ def lib():
             L.orc_spectrum.argtypes = [_P(Params), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                        _i64p, _f64p, _f64p, ctypes.c_int32, ctypes.c_int32, _f64p]
             L.orc_spectrum.restype = ctypes.c_int
+            L.orc_fall.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _f64p]
+            L.orc_fall.restype = ctypes.c_int32
+            L.orc_fall_distance.argtypes = [_P(Params), ctypes.c_double]
+            L.orc_fall_distance.restype = ctypes.c_double
+            L.orc_sediment.argtypes = [_P(Params), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       _i64p, _f64p, _i32p, _f64p, _f64p]
+            L.orc_sediment.restype = ctypes.c_int
+            L.orc_zeta_of.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
+            L.orc_zeta_of.restype = ctypes.c_double
+            L.orc_z_of.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
+            L.orc_z_of.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -276,3 +287,40 @@ def spectrum(P: Params, st: State, edges, per_cell=False) -> np.ndarray:
     _check(lib().orc_spectrum(ctypes.byref(P), n, nc, ni, cp, ip, xp, vp, _ptr(e, ctypes.c_double),
                               len(e), int(bool(per_cell)), _ptr(out, ctypes.c_double)), "spectrum")
     return out.reshape(st.n_cells * st.n_inst, nb) if per_cell else out
+
+
+# -------------------------------------------------------------- sedimentation
+def fall(zeta, iz, d, dz):
+    """(new level or -1, new zeta) of one SD falling d in one step."""
+    out = ctypes.c_double()
+    lvl = lib().orc_fall(float(zeta), int(iz), float(d), float(dz), ctypes.byref(out))
+    return int(lvl), out.value
+
+
+def fall_distance(P: Params, v):
+    return lib().orc_fall_distance(ctypes.byref(P), float(v))
+
+
+def zeta_of(z, cell, nx, dz):
+    """Heights above the cells' bottoms from heights above the domain bottom."""
+    f = lib().orc_zeta_of
+    return np.array([f(float(a), int(c), int(nx), float(dz)) for a, c in zip(np.ravel(z), np.ravel(cell))])
+
+
+def z_of(zeta, cell, nx, dz):
+    f = lib().orc_z_of
+    return np.array([f(float(a), int(c), int(nx), float(dz)) for a, c in zip(np.ravel(zeta), np.ravel(cell))])
+
+
+def sediment(P: Params, st: State, nx: int, dz: float, zeta: np.ndarray) -> float:
+    """One sedimentation step in place (st.cell and zeta); returns the
+    precipitated volume sum(xi v) of the SDs that fell through the bottom."""
+    if st.inst is not None:
+        raise ValueError("sedimentation of a single instance only")
+    n, nc, ni, cp, ip, xp, vp = st._args()
+    if zeta.dtype != np.float64 or not zeta.flags.c_contiguous or len(zeta) != n:
+        raise ValueError("zeta must be a contiguous float64 array of n_sd heights")
+    pr = ctypes.c_double(0.0)
+    _check(lib().orc_sediment(ctypes.byref(P), n, int(nx), nc, float(dz), xp, vp, cp,
+                              _ptr(zeta, ctypes.c_double), ctypes.byref(pr)), "sediment")
+    return pr.value

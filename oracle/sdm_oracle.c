@@ -25,6 +25,14 @@
  * result bit for bit.  All floating point is IEEE binary64/binary32 with
  * round-to-nearest and no contraction: build with -ffp-contract=off.
  *
+ * Sedimentation (a next step of the method, paper: API in brief, the
+ * "particle displacement" dynamic; Usage examples, the 2-D example's
+ * sedimenting drizzle): every live SD falls by its Rogers-Yau fall speed
+ * times dt.  Cells are levels x columns (cell = iz * nx + ix, levels of
+ * height dz); an SD's position is its height zeta above its cell's bottom.
+ * SDs falling through the bottom leave the domain (cell -1: outside, never
+ * stepped) and their water is precipitated; dead SDs leave it as well.
+ *
  * Parity status: every function below is pinned by tests/test_oracle_*.py
  * (Philox known answers, hand-worked Shima pairs, brute-force pairing and
  * gamma frequencies, volume conservation, the Golovin closed form).  The
@@ -372,12 +380,16 @@ static int group_sds(int64_t n_sd, int32_t n_cells, int32_t n_inst, const int32_
         return ORC_ENOMEM;
     }
     for (int64_t i = 0; i < n_sd; ++i) {
+        if (cell[i] < 0)
+            continue; /* outside the domain */
         int64_t g = (int64_t)(inst ? inst[i] : 0) * n_cells + cell[i];
         start[g + 1] += 1;
     }
     for (int64_t g = 0; g < n_groups; ++g)
         start[g + 1] += start[g];
     for (int64_t i = 0; i < n_sd; ++i) {
+        if (cell[i] < 0)
+            continue;
         int64_t g = (int64_t)(inst ? inst[i] : 0) * n_cells + cell[i];
         members[start[g] + fill[g]] = i;
         fill[g] += 1;
@@ -394,7 +406,7 @@ static int check_layout(int64_t n_sd, int32_t n_cells, int32_t n_inst, const int
     if (n_sd < 0 || n_cells < 1 || n_inst < 1)
         return ORC_EINVAL;
     for (int64_t i = 0; i < n_sd; ++i) {
-        if (cell[i] < 0 || cell[i] >= n_cells)
+        if (cell[i] < -1 || cell[i] >= n_cells) /* -1: outside the domain */
             return ORC_EINVAL;
         if (inst && (inst[i] < 0 || inst[i] >= n_inst))
             return ORC_EINVAL;
@@ -545,7 +557,7 @@ int orc_spectrum(const orc_params *P, int64_t n_sd, int32_t n_cells, int32_t n_i
     for (int64_t q = 0; q < n_out; ++q)
         out[q] = 0.0;
     for (int64_t i = 0; i < n_sd; ++i) {
-        if (xi[i] <= 0)
+        if (xi[i] <= 0 || cell[i] < 0)
             continue;
         double r = orc_radius(v[i]);
         if (r < edges[0] || !(r < edges[n_edges - 1]))
@@ -569,3 +581,78 @@ int orc_spectrum(const orc_params *P, int64_t n_sd, int32_t n_cells, int32_t n_i
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------ sedimentation */
+/* The fall of one SD in one step: its height zeta above the bottom of level
+ * iz drops by d; each time it goes below zero the SD enters the level below,
+ * whose top it reaches with zeta + dz.  Returns the new level (-1: through
+ * the bottom of the domain) and writes the new zeta.  If zeta + dz rounds up
+ * to dz itself, the SD is on the boundary and stays in the level above, at
+ * zeta = 0 (levels are half-open [iz dz, (iz + 1) dz)). */
+int32_t orc_fall(double zeta, int32_t iz, double d, double dz, double *zeta_out)
+{
+    double z = zeta - d;
+    while (z < 0.0) {
+        iz -= 1;
+        if (iz < 0) {
+            *zeta_out = 0.0;
+            return -1;
+        }
+        z = z + dz;
+    }
+    if (z >= dz) {
+        iz += 1;
+        z = 0.0;
+    }
+    *zeta_out = z;
+    return iz;
+}
+
+/* The fall distance of one step: the Rogers-Yau speed of the binary32
+ * radius twin, times dt, in binary32 (the speed formula itself is good to
+ * some per cent), widened exactly to binary64. */
+double orc_fall_distance(const orc_params *P, double v)
+{
+    float r = orc_radiusf((float)v);
+    float vt = orc_vtf(P, r);
+    return (double)(vt * (float)P->dt);
+}
+
+/* One sedimentation step over every SD, in SD-id order.  cell, zeta are
+ * updated in place; *precip (if given) is increased by xi v of every SD that
+ * falls through the bottom (summed in id order).  Dead SDs (xi = 0) and SDs
+ * already outside end up outside (cell -1, zeta 0). */
+int orc_sediment(const orc_params *P, int64_t n_sd, int32_t nx, int32_t n_cells, double dz,
+                 const int64_t *xi, const double *v, int32_t *cell, double *zeta, double *precip)
+{
+    if (nx < 1 || n_cells % nx != 0 || !(dz > 0.0))
+        return ORC_EINVAL;
+    int rc = check_layout(n_sd, n_cells, 1, cell, NULL);
+    if (rc != ORC_OK)
+        return rc;
+    for (int64_t i = 0; i < n_sd; ++i) {
+        if (cell[i] < 0 || xi[i] <= 0) {
+            cell[i] = -1;
+            zeta[i] = 0.0;
+            continue;
+        }
+        int32_t iz = cell[i] / nx, ix = cell[i] % nx;
+        double d = orc_fall_distance(P, v[i]);
+        iz = orc_fall(zeta[i], iz, d, dz, &zeta[i]);
+        if (iz < 0) {
+            if (precip)
+                *precip += (double)xi[i] * v[i];
+            cell[i] = -1;
+            continue;
+        }
+        cell[i] = iz * nx + ix;
+    }
+    return ORC_OK;
+}
+
+/* Height above the cell's bottom from the height above the domain bottom,
+ * and back: zeta = z - iz dz, z = iz dz + zeta (binary64, each product and
+ * sum rounded once). */
+double orc_zeta_of(double z, int32_t cell, int32_t nx, double dz) { return z - (double)(cell / nx) * dz; }
+
+double orc_z_of(double zeta, int32_t cell, int32_t nx, double dz) { return (double)(cell / nx) * dz + zeta; }
