@@ -108,9 +108,12 @@ sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_str
  * which addresses its random sort key).
  *   xi[n_sd]      int64 multiplicity, >= 0 (0 marks a dead SD)
  *   volume[n_sd]  binary64 volume in m^3, finite, in [1e-30, 1e30]
- *   cell_id[n_sd] int32 cell in [0, n_cells)
- * n_sd in [1, capacity_sd].  Replaces any earlier state; the step counter is
- * kept.  Errors: SDM_EINVAL (names the first offending SD), SDM_ECUDA. */
+ *   cell_id[n_sd] int32 cell in [0, n_cells), or -1: outside the domain (an
+ *                 SD that has fallen through its bottom; kept, never stepped,
+ *                 not counted by sdm_spectrum)
+ * n_sd in [1, capacity_sd].  Replaces any earlier state, including positions
+ * (sdm_set_positions); the step counter is kept.  Errors: SDM_EINVAL (names
+ * the first offending SD), SDM_ECUDA. */
 sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, const double *volume,
                               const int32_t *cell_id, int on_device);
 
@@ -186,12 +189,52 @@ sdm_status sdm_batch_create(sdm_ctx *const *ctxs, int32_t n_ctx, void *cuda_stre
 
 /* Enqueues n_steps steps of every context in the batch on the batch's
  * stream; the contexts' streams are not used.  Errors: SDM_EINVAL,
- * SDM_ESTATE, SDM_ECUDA. */
+ * SDM_ESTATE (also when a context's layout changed since the batch was
+ * created: sdm_set_attributes or sdm_sedimentation_step), SDM_ECUDA. */
 sdm_status sdm_batch_step(sdm_batch *batch, int32_t n_steps);
 
 sdm_status sdm_batch_destroy(sdm_batch *batch);
 
 const char *sdm_batch_last_error(const sdm_batch *batch);
+
+/* ---- sedimentation (a next step of the method: the paper's "particle
+ * displacement" dynamic and the sedimenting drizzle of its 2-D example; the
+ * paper prints no formulae).  Cells are levels x columns: cell c lies in
+ * level iz = c / nx and column ix = c mod nx, level iz spans heights
+ * [iz dz, (iz + 1) dz) above the domain bottom.  Each SD's position is kept
+ * as its height zeta above its cell's bottom (binary64).
+ *
+ * One sedimentation step, for every live SD: d = v_t(r) dt in binary32 (the
+ * Rogers-Yau speed of the binary32 radius of the binary32 image of the
+ * volume, the twin used by SDM_PREC_KFP32, times (float)dt), widened exactly
+ * to binary64; zeta -= d; while zeta < 0 the SD enters the level below
+ * (zeta += dz).  An SD that goes below level 0 leaves the domain (cell -1)
+ * and its xi v is precipitated; if zeta + dz rounds up to dz the SD stays in
+ * the level above at zeta = 0.  Dead SDs (xi = 0) leave the domain too.
+ * Columns never change.  Afterwards cells hold their SDs in increasing id
+ * again, so the next coalescence step sees the new cell membership. */
+
+/* Sets the positions: z[n_sd] (SD-id order, host or device) the height of
+ * each SD above the domain bottom, m.  Needs attributes; nx >= 1 divides
+ * n_cells; dz > 0 finite.  Each SD's zeta = z - (c / nx) dz (binary64) must
+ * lie in [0, dz); SDs outside the domain ignore z.  Errors: SDM_EINVAL (names
+ * the first offending SD), SDM_ESTATE (no attributes), SDM_ENOMEM,
+ * SDM_ECUDA.  Synchronises the context's stream. */
+sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device);
+
+/* One sedimentation step (asynchronous up to one host read of the new cell
+ * offsets; stream-ordered with the coalescence steps).  precipitated
+ * (nullable host pointer) receives sum(xi v), m^3, of the SDs that fell
+ * through the bottom in this step.  A batch (sdm_batch_create) holding the
+ * context must be created again afterwards: its next step fails with
+ * SDM_ESTATE.  Errors: SDM_ESTATE (no positions), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated);
+
+/* Positions in SD-id order: z[n_sd] (nullable; needs positions) the height
+ * above the domain bottom, (c / nx) dz + zeta in binary64, 0 for SDs outside
+ * the domain; cell[n_sd] (nullable) the SD's cell, -1 outside.  Host
+ * arrays: synchronises; device arrays: stream-ordered. */
+sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, int on_device);
 
 /* ---- launch tuning.  Which cells are sorted in shared memory (the rest take
  * the multi-pass global path), which run one warp per cell, and how many

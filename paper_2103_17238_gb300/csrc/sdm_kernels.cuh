@@ -1312,10 +1312,11 @@ __global__ void spectrum_finalize_kernel(const double *__restrict__ acc, const d
 }
 
 // --------------------------------------------------------------- layout
-// Validation and per-cell counts of set_attributes.  flags bit 0: an
-// invalid attribute (first bad SD index in *bad); bit 1: cells not sorted.
+// Validation and per-group counts of set_attributes (groups: the cells, then
+// n_cells for the SDs outside the domain, cell id -1).  flags bit 0: an
+// invalid attribute (first bad SD index in *bad); bit 1: groups not sorted.
 // Each warp takes 32 consecutive SDs at a time and adds one count per run of
-// equal cell ids (one or two atomics per warp for cell-sorted input).
+// equal groups (one or two atomics per warp for sorted input).
 __global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
                                       const int32_t *__restrict__ cell, int32_t n_cells, uint32_t *__restrict__ counts,
                                       uint32_t *__restrict__ flags, unsigned long long *__restrict__ bad)
@@ -1326,11 +1327,12 @@ __global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ 
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_sd; base += wstride) {
         const int64_t i = base + lane;
         const bool in = i < n_sd;
-        const int32_t craw = in ? cell[i] : INT32_MAX;
-        int32_t c = -1; // counted cell, -1: none
+        const int32_t c_in = in ? cell[i] : INT32_MAX;
+        const int32_t craw = c_in == -1 ? n_cells : c_in; // the group; outside sorts last
+        int32_t c = -1;                                     // counted group, -1: none
         if (in) {
             const double vi = v[i];
-            if (xi[i] >= 0 && vi >= 1e-30 && vi <= 1e30 && craw >= 0 && craw < n_cells) {
+            if (xi[i] >= 0 && vi >= 1e-30 && vi <= 1e30 && c_in >= -1 && c_in < n_cells) {
                 c = craw;
             } else {
                 atomicOr(flags, 1u);
@@ -1338,8 +1340,11 @@ __global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ 
             }
         }
         int32_t prev = __shfl_up_sync(FULL, craw, 1);
-        if (lane == 0)
-            prev = (in && i > 0) ? cell[i - 1] : INT32_MIN;
+        if (lane == 0) {
+            prev = INT32_MIN;
+            if (in && i > 0)
+                prev = cell[i - 1] == -1 ? n_cells : cell[i - 1];
+        }
         if (__any_sync(FULL, in && prev > craw) && lane == 0)
             atomicOr(flags, 2u);
         const int32_t next = __shfl_down_sync(FULL, c, 1);
@@ -1353,10 +1358,11 @@ __global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ 
     }
 }
 
-// Cell-sorted input: SD i goes to padded slot poff[c] + (i - uoff[c]).
-// Otherwise pos[i] gives the slot.
+// Group-sorted input: SD i goes to padded slot poff[g] + (i - uoff[g]), g its
+// group (cell id -1: n_cells, outside the domain).  Otherwise pos[i] gives
+// the slot.
 __global__ void scatter_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
-                               const int32_t *__restrict__ cell, const int32_t *__restrict__ poff,
+                               const int32_t *__restrict__ cell, int32_t n_cells, const int32_t *__restrict__ poff,
                                const int32_t *__restrict__ uoff, const int32_t *__restrict__ pos,
                                int64_t *__restrict__ sxi, double *__restrict__ sv, int32_t *__restrict__ id_of_slot)
 {
@@ -1365,7 +1371,7 @@ __global__ void scatter_kernel(int64_t n_sd, const int64_t *__restrict__ xi, con
         if (pos) {
             p = pos[i];
         } else {
-            const int32_t c = cell[i];
+            const int32_t c = cell[i] < 0 ? n_cells : cell[i];
             p = poff[c] + (int32_t)(i - uoff[c]);
         }
         sxi[p] = xi[i];
@@ -1374,7 +1380,7 @@ __global__ void scatter_kernel(int64_t n_sd, const int64_t *__restrict__ xi, con
     }
 }
 
-// Padding slots (the one slot after an odd cell): dead, with a harmless
+// Padding slots (the one slot after an odd group): dead, with a harmless
 // positive volume.
 __global__ void fill_padding_kernel(int32_t n_cells, const int32_t *__restrict__ poff, const int32_t *__restrict__ uoff,
                                     int64_t *__restrict__ sxi, double *__restrict__ sv, int32_t *__restrict__ id_of_slot)

@@ -83,6 +83,8 @@ struct Plan {
     sdm_tuning tuning{}; // the launch tuning the plan was built with
 };
 
+struct SedBuffers; // second layout and scratch of the sedimentation step (sdm_sediment.cu)
+
 } // namespace
 
 struct sdm_ctx {
@@ -98,6 +100,13 @@ struct sdm_ctx {
     int32_t largest_cell = 0;
     bool has_attributes = false;
     bool broken = false;
+    int64_t layout_version = 0; // changes with every new layout (batches check it)
+    // sedimentation: positions set by sdm_set_positions, buffers at first use
+    bool has_positions = false;
+    int32_t nx = 0;
+    double dz = 0.0;
+    double *d_zeta = nullptr; // height above the cell's bottom, per slot
+    SedBuffers *sed = nullptr;
     std::string error;
     // device state
     int64_t *d_xi = nullptr;
@@ -110,6 +119,10 @@ struct sdm_ctx {
     sdm_batch *self_batch = nullptr;
 };
 
+namespace {
+void sed_release(sdm_ctx *ctx); // frees the sedimentation buffers (sdm_sediment.cu)
+} // namespace
+
 struct sdm_batch {
     std::vector<sdm_ctx *> ctxs;
     cudaStream_t stream = nullptr;
@@ -121,6 +134,7 @@ struct sdm_batch {
     cudaStream_t capture_stream = nullptr;
     int64_t *d_delta = nullptr;       // per-run step deltas for counter syncs
     std::vector<int64_t> h_delta;
+    std::vector<int64_t> versions;    // the contexts' layout versions the plan was built for
     std::string error;
     bool broken = false;
 };
@@ -492,6 +506,7 @@ sdm_status batch_init(sdm_batch *b, sdm_ctx *const *ctxs, int32_t n_ctx, cudaStr
         if (!ctxs[i]->has_attributes)
             return fail(&b->error, SDM_ESTATE, "context %d has no attributes", i);
         b->ctxs.push_back(ctxs[i]);
+        b->versions.push_back(ctxs[i]->layout_version);
     }
     b->stream = stream;
     b->mem = ctxs[0]->mem;
@@ -528,9 +543,14 @@ sdm_status batch_step(sdm_batch *b, int32_t n_steps)
         return fail(&b->error, SDM_ESTATE, "batch unusable after a CUDA error");
     if (n_steps < 0)
         return fail(&b->error, SDM_EINVAL, "n_steps < 0");
-    for (sdm_ctx *c : b->ctxs)
-        if (c->broken)
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if (b->ctxs[i]->broken)
             return fail(&b->error, SDM_ESTATE, "a context of the batch is unusable");
+        if (b->ctxs[i]->layout_version != b->versions[i])
+            return fail(&b->error, SDM_ESTATE,
+                        "context %zu has a new layout (set_attributes or a sedimentation step): create the batch again",
+                        i);
+    }
     if (n_steps == 0)
         return SDM_OK;
     int32_t left = n_steps;
@@ -687,8 +707,8 @@ void sdm_config_default(sdm_config *cfg)
 
 int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t largest_cell)
 {
-    const int64_t slots = capacity_sd + n_cells;
-    int64_t bytes = slots * (8 + 8 + 4) + ((int64_t)n_cells + 1) * 4 + (int64_t)sizeof(InstDev);
+    const int64_t slots = capacity_sd + n_cells + 1;
+    int64_t bytes = slots * (8 + 8 + 4) + ((int64_t)n_cells + 2) * 4 + (int64_t)sizeof(InstDev);
     if (largest_cell > current_tuning().smem_max_sd) {
         // big-cell scratch, at most: keys, ranks, perm per SD; counts per chunk and bucket
         const int lb = big_lb(largest_cell);
@@ -705,8 +725,8 @@ sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_str
     sdm_status st = check_config(cfg, nullptr);
     if (st != SDM_OK)
         return st;
-    if (capacity_sd < 1 || capacity_sd + cfg->n_cells > (int64_t)INT32_MAX)
-        return fail(nullptr, SDM_EINVAL, "capacity_sd must be in [1, 2^31 - 1 - n_cells]");
+    if (capacity_sd < 1 || capacity_sd + cfg->n_cells + 1 > (int64_t)INT32_MAX)
+        return fail(nullptr, SDM_EINVAL, "capacity_sd must be in [1, 2^31 - 2 - n_cells]");
     sdm_ctx *c = new (std::nothrow) sdm_ctx();
     if (!c)
         return fail(nullptr, SDM_ENOMEM, "host allocation failed");
@@ -717,14 +737,14 @@ sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_str
     c->mem.user = cfg->alloc_user;
     c->mem.stream = c->stream;
     c->capacity_sd = capacity_sd;
-    c->n_slots_cap = capacity_sd + cfg->n_cells;
+    c->n_slots_cap = capacity_sd + cfg->n_cells + 1; // every group (cells, outside) padded to even
     c->step = cfg->step0;
     c->d_xi = (int64_t *)c->mem.get(sizeof(int64_t) * c->n_slots_cap);
     c->d_v = (double *)c->mem.get(sizeof(double) * c->n_slots_cap);
     c->d_id_of_slot = (int32_t *)c->mem.get(sizeof(int32_t) * c->n_slots_cap);
-    c->d_cell_off = (int32_t *)c->mem.get(sizeof(int32_t) * (cfg->n_cells + 1));
+    c->d_cell_off = (int32_t *)c->mem.get(sizeof(int32_t) * (cfg->n_cells + 2));
     c->d_inst = (InstDev *)c->mem.get(sizeof(InstDev));
-    c->device_bytes = c->n_slots_cap * 20 + (int64_t)(cfg->n_cells + 1) * 4 + (int64_t)sizeof(InstDev);
+    c->device_bytes = c->n_slots_cap * 20 + (int64_t)(cfg->n_cells + 2) * 4 + (int64_t)sizeof(InstDev);
     if (!c->d_xi || !c->d_v || !c->d_id_of_slot || !c->d_cell_off || !c->d_inst) {
         sdm_destroy(c);
         return fail(nullptr, SDM_ENOMEM, "device allocation of %lld SDs failed", (long long)capacity_sd);
@@ -766,24 +786,26 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
         dv = (const double *)(p + b_xi);
         dcell = (const int32_t *)(p + b_xi + b_v);
     }
-    // counts, flags, first bad index
-    const size_t b_counts = sizeof(uint32_t) * n_cells + 16;
+    // counts per group (the cells, then the SDs outside the domain), flags,
+    // first bad index
+    const int32_t n_groups = n_cells + 1;
+    const size_t b_counts = sizeof(uint32_t) * n_groups + 16;
     void *meta = mem.get(b_counts);
     if (!meta) {
         mem.put(stage, b_stage);
         return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
     }
     uint32_t *d_counts = (uint32_t *)meta;
-    uint32_t *d_flags = d_counts + n_cells;
+    uint32_t *d_flags = d_counts + n_groups;
     unsigned long long *d_bad = (unsigned long long *)(((uintptr_t)(d_flags + 1) + 7) & ~(uintptr_t)7);
     // d_bad lies inside the 16 spare bytes after the counts
     CTX_CUDA(ctx, cudaMemsetAsync(meta, 0, b_counts, s));
     CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
     validate_count_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_counts, d_flags, d_bad);
-    std::vector<uint32_t> counts(n_cells);
+    std::vector<uint32_t> counts(n_groups);
     uint32_t flags = 0;
     unsigned long long bad = 0;
-    CTX_CUDA(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * n_cells, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * n_groups, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaMemcpyAsync(&flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
@@ -791,21 +813,23 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
         mem.put(meta, b_counts);
         mem.put(stage, b_stage);
         return fail(&ctx->error, SDM_EINVAL,
-                    "SD %llu: need xi >= 0, volume in [1e-30, 1e30] m^3, cell in [0, %d)", bad, n_cells);
+                    "SD %llu: need xi >= 0, volume in [1e-30, 1e30] m^3, cell in [-1, %d)", bad, n_cells);
     }
-    // padded layout: every cell starts at an even slot
-    std::vector<int32_t> poff(n_cells + 1), uoff(n_cells + 1);
+    // padded layout: every group starts at an even slot; the SDs outside the
+    // domain follow the last cell
+    std::vector<int32_t> poff(n_groups + 1), uoff(n_groups + 1);
     int64_t ps = 0, us = 0;
     int32_t largest = 0;
-    for (int32_t c = 0; c < n_cells; ++c) {
+    for (int32_t c = 0; c < n_groups; ++c) {
         poff[c] = (int32_t)ps;
         uoff[c] = (int32_t)us;
         ps += (counts[c] + 1) & ~1u;
         us += counts[c];
-        largest = std::max<int32_t>(largest, (int32_t)counts[c]);
+        if (c < n_cells)
+            largest = std::max<int32_t>(largest, (int32_t)counts[c]);
     }
-    poff[n_cells] = (int32_t)ps;
-    uoff[n_cells] = (int32_t)us;
+    poff[n_groups] = (int32_t)ps;
+    uoff[n_groups] = (int32_t)us;
     // slot positions for unsorted input (stable by id)
     std::vector<int32_t> pos;
     if (flags & 2u) {
@@ -819,9 +843,9 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
         pos.resize(n_sd);
         std::vector<int32_t> fill(poff.begin(), poff.end() - 1);
         for (int64_t i = 0; i < n_sd; ++i)
-            pos[i] = fill[hcell[i]]++;
+            pos[i] = fill[hcell[i] < 0 ? n_cells : hcell[i]]++;
     }
-    const size_t b_aux = sizeof(int32_t) * 2 * (n_cells + 1) + (pos.empty() ? 0 : b_c);
+    const size_t b_aux = sizeof(int32_t) * 2 * (n_groups + 1) + (pos.empty() ? 0 : b_c);
     void *aux = mem.get(b_aux);
     if (!aux) {
         mem.put(meta, b_counts);
@@ -829,20 +853,23 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
         return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
     }
     int32_t *d_poff = (int32_t *)aux;
-    int32_t *d_uoff = d_poff + (n_cells + 1);
-    int32_t *d_pos = pos.empty() ? nullptr : d_uoff + (n_cells + 1);
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_poff, poff.data(), sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_uoff, uoff.data(), sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
+    int32_t *d_uoff = d_poff + (n_groups + 1);
+    int32_t *d_pos = pos.empty() ? nullptr : d_uoff + (n_groups + 1);
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_poff, poff.data(), sizeof(int32_t) * (n_groups + 1), cudaMemcpyHostToDevice, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_uoff, uoff.data(), sizeof(int32_t) * (n_groups + 1), cudaMemcpyHostToDevice, s));
     if (d_pos)
         CTX_CUDA(ctx, cudaMemcpyAsync(d_pos, pos.data(), b_c, cudaMemcpyHostToDevice, s));
     // a context's own launch plan depends only on the padded layout and the
     // launch tuning: kept when both are unchanged
-    const bool keep_plan = ctx->self_batch && ctx->h_cell_off == poff &&
+    std::vector<int32_t> cell_off(poff.begin(), poff.begin() + n_cells + 1);
+    const bool keep_plan = ctx->self_batch && ctx->h_cell_off == cell_off &&
                            same_tuning(ctx->self_batch->plan.tuning, current_tuning());
     ctx->n_sd = n_sd;
     ctx->n_slots = ps;
     ctx->largest_cell = largest;
-    ctx->h_cell_off = poff;
+    ctx->h_cell_off = cell_off;
+    ctx->has_positions = false;
+    ctx->layout_version += 1;
     ctx->dev_base = ctx->step;
     InstDev inst = make_inst(ctx);
     // Copies from pageable memory wait for the stream's earlier work, so the
@@ -853,15 +880,17 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff.data(), sizeof(int32_t) * (n_cells + 1),
                                   cudaMemcpyHostToDevice, s));
     CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
-    fill_padding_kernel<<<(n_cells + 255) / 256, 256, 0, s>>>(n_cells, d_poff, d_uoff, ctx->d_xi, ctx->d_v,
-                                                               ctx->d_id_of_slot);
-    scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
+    fill_padding_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, d_poff, d_uoff, ctx->d_xi, ctx->d_v,
+                                                                ctx->d_id_of_slot);
+    scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
                                         ctx->d_id_of_slot);
     CTX_CUDA(ctx, cudaGetLastError());
     mem.put(aux, b_aux);
     mem.put(meta, b_counts);
     mem.put(stage, b_stage);
     ctx->has_attributes = true;
+    if (ctx->self_batch && keep_plan)
+        ctx->self_batch->versions[0] = ctx->layout_version;
     if (ctx->self_batch && !keep_plan) {
         batch_release(ctx->self_batch);
         delete ctx->self_batch;
@@ -936,7 +965,8 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, host_e.data(), b_edges, cudaMemcpyHostToDevice, s));
     const double vol = per_cell ? ctx->cfg.dv : ctx->cfg.dv * (double)ctx->cfg.n_cells;
     if (total) {
-        spectrum_total_kernel<<<grid, kSpecTotNT, 0, s>>>(ctx->d_inst, ctx->n_slots, d_edges, n_edges, d_acc);
+        spectrum_total_kernel<<<grid, kSpecTotNT, 0, s>>>(ctx->d_inst, ctx->h_cell_off[ctx->cfg.n_cells], d_edges,
+                                                          n_edges, d_acc);
         spectrum_total_finalize_kernel<<<nb, 32, 0, s>>>(d_acc, grid, d_dln, nb, vol, d_out);
     } else {
         CTX_CUDA(ctx, cudaMemsetAsync(d_acc, 0, b_acc, s));
@@ -1012,6 +1042,7 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     ctx->mem.put(ctx->d_id_of_slot, 0);
     ctx->mem.put(ctx->d_cell_off, 0);
     ctx->mem.put(ctx->d_inst, 0);
+    sed_release(ctx);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     delete ctx;
     if (e != cudaSuccess)
@@ -1102,4 +1133,5 @@ const char *sdm_batch_last_error(const sdm_batch *batch)
 } // extern "C"
 
 // The allocation-free entry point, after the kernels and helpers it uses.
+#include "sdm_sediment.cu"
 #include "sdm_noalloc.cu"

@@ -1,0 +1,585 @@
+// Sedimentation step (sdm_set_positions, sdm_sedimentation_step,
+// sdm_get_positions in include/sdm.h).
+//
+// The paper lists particle displacement among the dynamics of its framework
+// and shows sedimenting drizzle in its 2-D example; it prints no formulae.
+// Reading: every live SD falls by its Rogers-Yau speed times dt, the speed
+// taken from the binary32 radius twin of its volume (the KFP32 arithmetic)
+// and the distance widened exactly to binary64; positions are heights above
+// the bottom of the SD's cell, so a step needs no division.
+//
+// One step on the device:
+//   sed_move_kernel      warp per group (each cell, then the SDs outside the
+//                        domain): the fall, the new group of every SD as a
+//                        key in SD-id order, counts per new group, the water
+//                        that leaves through the bottom per cell;
+//   sed_scan_kernel      new group offsets (unpadded and padded to even
+//                        slots) and the precipitated total, in fixed order;
+//   radix_*_kernel       stable LSD radix sort of the keys (SD-id order in,
+//                        so equal groups keep increasing id);
+//   sed_gather_kernel    the new layout, gathered from the old one;
+//   sed_pad_kernel       its padding slots.
+// The two layouts swap; the host reads the new offsets for the launch plan.
+//
+// Compiled as part of the library's single translation unit (included at the
+// end of sdm_runtime.cu).
+
+namespace {
+
+constexpr int kSedNT = 256;
+constexpr int kRadixNT = 256;
+constexpr int kRadixRounds = 16;
+constexpr int kRadixTile = kRadixNT * kRadixRounds; // keys per block and pass
+constexpr int kRadixBuckets = 256;                  // 8-bit digits
+
+// ------------------------------------------------------------------ kernels
+// zeta of every slot from z (SD-id order): z - (c / nx) dz, which must lie
+// in [0, dz); flags bit 0 and the first bad id on failure.  SDs outside the
+// domain and padding slots get zeta 0.
+__global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restrict__ cell_off, int32_t n_cells,
+                                                         int64_t n_slots, const int32_t *__restrict__ id_of_slot,
+                                                         const double *__restrict__ z, int32_t nx, double dz,
+                                                         double *__restrict__ zeta, uint32_t *__restrict__ flags,
+                                                         unsigned long long *__restrict__ bad)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = gw; g <= n_cells; g += nw) {
+        const int64_t lo = cell_off[g], hi = g < n_cells ? cell_off[g + 1] : n_slots;
+        const double base = __dmul_rn((double)(g / nx), dz);
+        for (int64_t s = lo + lane; s < hi; s += 32) {
+            const int32_t id = id_of_slot[s];
+            double zt = 0.0;
+            if (id >= 0 && g < n_cells) {
+                zt = __dsub_rn(z[id], base);
+                if (!(zt >= 0.0 && zt < dz)) {
+                    atomicOr(flags, 1u);
+                    atomicMin(bad, (unsigned long long)id);
+                    zt = 0.0;
+                }
+            }
+            zeta[s] = zt;
+        }
+    }
+}
+
+// z[id] = (c / nx) dz + zeta (0 outside) and cell[id] = c (-1 outside).
+__global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restrict__ cell_off, int32_t n_cells,
+                                                         int64_t n_slots, const int32_t *__restrict__ id_of_slot,
+                                                         const double *__restrict__ zeta, int32_t nx, double dz,
+                                                         double *__restrict__ z, int32_t *__restrict__ cell)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = gw; g <= n_cells; g += nw) {
+        const int64_t lo = cell_off[g], hi = g < n_cells ? cell_off[g + 1] : n_slots;
+        const double base = g < n_cells && z ? __dmul_rn((double)(g / nx), dz) : 0.0;
+        for (int64_t s = lo + lane; s < hi; s += 32) {
+            const int32_t id = id_of_slot[s];
+            if (id < 0)
+                continue;
+            if (z)
+                z[id] = g < n_cells ? __dadd_rn(base, zeta[s]) : 0.0;
+            if (cell)
+                cell[id] = g < n_cells ? g : -1;
+        }
+    }
+}
+
+// The fall of every SD.  key[id] = its new group (n_cells: outside),
+// val[id] = its slot, zeta_new[slot] = its new height; counts[new group]
+// (one atomic per run of equal groups in a warp's 32 slots); precip[c] =
+// sum of xi v of the SDs of cell c that fell through the bottom (slot order
+// per lane, then a fixed tree over lanes).
+__global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restrict__ P, int32_t n_cells, int64_t n_slots,
+                                                          int32_t nx, double dz, float dt32,
+                                                          const double *__restrict__ zeta,
+                                                          const int32_t *__restrict__ id_of_slot,
+                                                          uint32_t *__restrict__ key, uint32_t *__restrict__ val,
+                                                          double *__restrict__ zeta_new, uint32_t *__restrict__ counts,
+                                                          double *__restrict__ precip)
+{
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    const PairConsts C = pair_consts(P);
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int64_t *__restrict__ gxi = P->xi;
+    const double *__restrict__ gv = P->v;
+    for (int g = gw; g <= n_cells; g += nw) {
+        const int64_t lo = P->cell_off[g], hi = g < n_cells ? P->cell_off[g + 1] : n_slots;
+        const bool inside = g < n_cells;
+        const int32_t iz0 = inside ? g / nx : 0, ix = inside ? g % nx : 0;
+        double pr = 0.0;
+        for (int64_t s0 = lo; s0 < hi; s0 += 32) { // warp-uniform trip count
+            const int64_t s = s0 + lane;
+            const int32_t id = s < hi ? id_of_slot[s] : -1;
+            int32_t ng = -1; // -1: padding, nothing to count
+            if (id >= 0) {
+                const int64_t x = gxi[s];
+                double zn = 0.0;
+                ng = n_cells;
+                if (inside && x > 0) {
+                    const double vv = gv[s];
+                    bool in_range;
+                    const float vf = d2f_rn(vv, in_range);
+                    const double d = (double)__fmul_rn(vt32c(C, radius32(vf)), dt32);
+                    double zz = __dsub_rn(zeta[s], d);
+                    int32_t iz = iz0;
+                    while (zz < 0.0) { // at most as many levels as the SD falls through
+                        iz -= 1;
+                        if (iz < 0)
+                            break;
+                        zz = __dadd_rn(zz, dz);
+                    }
+                    if (iz < 0) {
+                        pr = __dadd_rn(pr, __dmul_rn(xi2d(x), vv));
+                    } else {
+                        if (zz >= dz) { // zeta + dz rounded up to dz: on the boundary, level above
+                            iz += 1;
+                            zz = 0.0;
+                        }
+                        ng = iz * nx + ix;
+                        zn = zz;
+                    }
+                }
+                key[id] = (uint32_t)ng;
+                val[id] = (uint32_t)s;
+                zeta_new[s] = zn;
+            }
+            const int32_t nxt = __shfl_down_sync(FULL, ng, 1);
+            const bool end = lane == 31 || nxt != ng;
+            const unsigned ends = __ballot_sync(FULL, end);
+            if (end && ng >= 0) {
+                const unsigned below = ends & ((1u << lane) - 1u);
+                const int start = below ? 32 - __clz(below) : 0;
+                atomicAdd(&counts[ng], (uint32_t)(lane - start + 1));
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+            pr = __dadd_rn(pr, __shfl_down_sync(FULL, pr, d));
+        if (lane == 0 && inside)
+            precip[g] = pr;
+    }
+}
+
+// One block: ustart = exclusive scan of counts[0 .. n_groups) (total at
+// ustart[n_groups]); poff the same with every count rounded up to even;
+// *precip_total = sum of precip[0 .. n_cells) in a fixed order.
+__global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restrict__ counts, int32_t n_groups,
+                                                        int32_t *__restrict__ ustart, int32_t *__restrict__ poff,
+                                                        const double *__restrict__ precip, int32_t n_cells,
+                                                        double *__restrict__ precip_total)
+{
+    __shared__ uint32_t s_u[1024], s_p[1024];
+    __shared__ uint32_t s_warp[32];
+    __shared__ double s_pr[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (n_groups + 1023) / 1024;
+    const int a = min(n_groups, t * per), b = min(n_groups, a + per);
+    uint32_t su = 0, sp = 0;
+    for (int g = a; g < b; ++g) {
+        su += counts[g];
+        sp += (counts[g] + 1u) & ~1u;
+    }
+    s_u[t] = su;
+    s_p[t] = sp;
+    __syncthreads();
+    const uint32_t tu = block_exclusive_scan<1024, 1024>(s_u, s_warp);
+    const uint32_t tp = block_exclusive_scan<1024, 1024>(s_p, s_warp);
+    uint32_t ru = s_u[t], rp = s_p[t];
+    for (int g = a; g < b; ++g) {
+        ustart[g] = (int32_t)ru;
+        poff[g] = (int32_t)rp;
+        ru += counts[g];
+        rp += (counts[g] + 1u) & ~1u;
+    }
+    if (t == 0) {
+        ustart[n_groups] = (int32_t)tu;
+        poff[n_groups] = (int32_t)tp;
+    }
+    const int pper = (n_cells + 1023) / 1024;
+    const int pa = min(n_cells, t * pper), pb = min(n_cells, pa + pper);
+    double pr = 0.0;
+    for (int c = pa; c < pb; ++c)
+        pr = __dadd_rn(pr, precip[c]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        pr = __dadd_rn(pr, __shfl_down_sync(0xFFFFFFFFu, pr, d));
+    if (lane == 0)
+        s_pr[warp] = pr;
+    __syncthreads();
+    if (warp == 0) {
+        pr = s_pr[lane];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+            pr = __dadd_rn(pr, __shfl_down_sync(0xFFFFFFFFu, pr, d));
+        if (lane == 0)
+            *precip_total = pr;
+    }
+}
+
+// hist[d * n_tiles + tile] = keys of the tile whose digit (key >> shift) & 255 is d.
+__global__ void __launch_bounds__(kRadixNT) radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                              uint32_t *__restrict__ hist, int32_t n_tiles)
+{
+    __shared__ uint32_t h[kRadixBuckets];
+    const int t = threadIdx.x;
+    h[t] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        const int64_t i = base + (int64_t)r * kRadixNT + t;
+        if (i < n)
+            atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)t * n_tiles + blockIdx.x] = h[t];
+}
+
+// One block: exclusive scan of a[0 .. n) in place.
+__global__ void __launch_bounds__(1024) scan_inplace_kernel(uint32_t *__restrict__ a, int64_t n)
+{
+    __shared__ uint32_t s[1024];
+    __shared__ uint32_t s_warp[32];
+    const int t = threadIdx.x;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t lo = min(n, (int64_t)t * per), hi = min(n, lo + per);
+    uint32_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i)
+        sum += a[i];
+    s[t] = sum;
+    __syncthreads();
+    block_exclusive_scan<1024, 1024>(s, s_warp);
+    uint32_t run = s[t];
+    for (int64_t i = lo; i < hi; ++i) {
+        const uint32_t x = a[i];
+        a[i] = run;
+        run += x;
+    }
+}
+
+// Stable scatter of one pass: tile keys in index order (round-major, thread
+// minor); within a round, lanes of a warp with equal digits are ranked by
+// __match_any_sync, warps by their per-digit counts in shared memory.
+__global__ void __launch_bounds__(kRadixNT) radix_scatter_kernel(const uint32_t *__restrict__ keys_in,
+                                                                 const uint32_t *__restrict__ vals_in, int64_t n,
+                                                                 int shift, const uint32_t *__restrict__ offs,
+                                                                 int32_t n_tiles, uint32_t *__restrict__ keys_out,
+                                                                 uint32_t *__restrict__ vals_out)
+{
+    constexpr int NW = kRadixNT / 32;
+    __shared__ uint32_t s_base[kRadixBuckets + 1];
+    __shared__ uint32_t s_wcnt[NW][kRadixBuckets + 1];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    s_base[t] = offs[(int64_t)t * n_tiles + blockIdx.x];
+    for (int i = t; i < NW * (kRadixBuckets + 1); i += kRadixNT)
+        (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        const int64_t i = base + (int64_t)r * kRadixNT + t;
+        const bool valid = i < n;
+        const uint32_t k = valid ? keys_in[i] : 0u;
+        const uint32_t v = valid ? vals_in[i] : 0u;
+        const uint32_t d = valid ? ((k >> shift) & 255u) : (uint32_t)kRadixBuckets;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t rank = (uint32_t)__popc(peers & lt);
+        if (rank == 0)
+            s_wcnt[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w)
+                before += s_wcnt[w][d];
+            const uint32_t pos = s_base[d] + before + rank;
+            keys_out[pos] = k;
+            vals_out[pos] = v;
+        }
+        __syncthreads();
+        for (int dd = t; dd <= kRadixBuckets; dd += kRadixNT) {
+            uint32_t sum = 0;
+            for (int w = 0; w < NW; ++w) {
+                sum += s_wcnt[w][dd];
+                s_wcnt[w][dd] = 0;
+            }
+            if (dd < kRadixBuckets)
+                s_base[dd] += sum;
+        }
+        __syncthreads();
+    }
+}
+
+// The new layout: the j-th SD in (group, id) order goes to slot
+// poff[g] + (j - ustart[g]).
+__global__ void sed_gather_kernel(int64_t n_sd, const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                                  const int32_t *__restrict__ ustart, const int32_t *__restrict__ poff,
+                                  const int64_t *__restrict__ xi, const double *__restrict__ v,
+                                  const double *__restrict__ zeta_new, const int32_t *__restrict__ id_of_slot,
+                                  int64_t *__restrict__ xi2, double *__restrict__ v2, double *__restrict__ zeta2,
+                                  int32_t *__restrict__ id2)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_sd; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = keys[j], s = vals[j];
+        const int64_t p = poff[g] + (j - ustart[g]);
+        xi2[p] = xi[s];
+        v2[p] = v[s];
+        zeta2[p] = zeta_new[s];
+        id2[p] = id_of_slot[s];
+    }
+}
+
+// The padding slot after every odd group of the new layout.
+__global__ void sed_pad_kernel(int32_t n_groups, const int32_t *__restrict__ ustart, const int32_t *__restrict__ poff,
+                               int64_t *__restrict__ xi2, double *__restrict__ v2, double *__restrict__ zeta2,
+                               int32_t *__restrict__ id2)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
+        for (int32_t p = poff[g] + (ustart[g + 1] - ustart[g]); p < poff[g + 1]; ++p) {
+            xi2[p] = 0;
+            v2[p] = 1.0;
+            zeta2[p] = 0.0;
+            id2[p] = -1;
+        }
+    }
+}
+
+// -------------------------------------------------------------------- host
+// The second layout (swapped with the context's after every step, so both
+// sets are freed through their current pointers) and the scratch.
+struct SedBuffers {
+    int64_t *xi2 = nullptr;
+    double *v2 = nullptr;
+    double *zeta2 = nullptr;
+    int32_t *id2 = nullptr;
+    int32_t *cell_off2 = nullptr; // n_cells + 2
+    double *zeta_new = nullptr;   // per slot of the old layout
+    uint32_t *keys[2] = {};
+    uint32_t *vals[2] = {};
+    uint32_t *counts = nullptr; // n_cells + 1
+    int32_t *ustart = nullptr;  // n_cells + 2
+    double *precip = nullptr;   // n_cells + 1 (the last: the total)
+    uint32_t *hist = nullptr;   // 256 x tiles
+    uint32_t *flags = nullptr;  // flags, then the first bad id (8-byte aligned)
+};
+
+void sed_release(sdm_ctx *ctx)
+{
+    if (ctx->sed) {
+        SedBuffers &b = *ctx->sed;
+        void *bufs[] = {b.xi2,     b.v2,      b.zeta2,  b.id2,    b.cell_off2, b.zeta_new, b.keys[0], b.keys[1],
+                        b.vals[0], b.vals[1], b.counts, b.ustart, b.precip,    b.hist,     b.flags};
+        for (void *p : bufs)
+            ctx->mem.put(p, 0);
+        delete ctx->sed;
+        ctx->sed = nullptr;
+    }
+    ctx->mem.put(ctx->d_zeta, 0);
+    ctx->d_zeta = nullptr;
+}
+
+template <typename T>
+T *sed_get(sdm_ctx *ctx, size_t count)
+{
+    return static_cast<T *>(ctx->mem.get(sizeof(T) * (count > 0 ? count : 1)));
+}
+
+sdm_status sed_alloc(sdm_ctx *ctx)
+{
+    if (ctx->sed)
+        return SDM_OK;
+    ctx->sed = new (std::nothrow) SedBuffers();
+    if (!ctx->sed)
+        return fail(&ctx->error, SDM_ENOMEM, "host allocation failed");
+    SedBuffers &b = *ctx->sed;
+    const int64_t slots = ctx->n_slots_cap, cap = ctx->capacity_sd;
+    const int32_t nc = ctx->cfg.n_cells;
+    const int64_t tiles = (cap + kRadixTile - 1) / kRadixTile;
+    ctx->d_zeta = (double *)ctx->mem.get(sizeof(double) * slots);
+    b.xi2 = sed_get<int64_t>(ctx, slots);
+    b.v2 = sed_get<double>(ctx, slots);
+    b.zeta2 = sed_get<double>(ctx, slots);
+    b.id2 = sed_get<int32_t>(ctx, slots);
+    b.cell_off2 = sed_get<int32_t>(ctx, (size_t)nc + 2);
+    b.zeta_new = sed_get<double>(ctx, slots);
+    for (int i = 0; i < 2; ++i) {
+        b.keys[i] = sed_get<uint32_t>(ctx, cap);
+        b.vals[i] = sed_get<uint32_t>(ctx, cap);
+    }
+    b.counts = sed_get<uint32_t>(ctx, (size_t)nc + 1);
+    b.ustart = sed_get<int32_t>(ctx, (size_t)nc + 2);
+    b.precip = sed_get<double>(ctx, (size_t)nc + 1);
+    b.hist = sed_get<uint32_t>(ctx, (size_t)kRadixBuckets * tiles + 1);
+    b.flags = sed_get<uint32_t>(ctx, 4);
+    const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.cell_off2 && b.zeta_new && b.keys[0] &&
+                    b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart && b.precip && b.hist && b.flags;
+    if (!ok) {
+        sed_release(ctx);
+        return fail(&ctx->error, SDM_ENOMEM, "sedimentation buffers: device allocation failed");
+    }
+    ctx->device_bytes += slots * (8 + 8 + 8 + 8 + 4 + 8) + cap * 16 + ((int64_t)nc + 2) * 24 +
+                         (int64_t)kRadixBuckets * tiles * 4;
+    return SDM_OK;
+}
+
+int sed_grid(int32_t n_groups)
+{
+    return std::max(1, std::min((n_groups + kSedNT / 32 - 1) / (kSedNT / 32), 152 * 16));
+}
+
+} // namespace
+
+extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_attributes has not been called");
+    const int32_t nc = ctx->cfg.n_cells;
+    if (!z || nx < 1 || nc % nx != 0 || !(std::isfinite(dz) && dz > 0.0))
+        return fail(&ctx->error, SDM_EINVAL, "need z, nx >= 1 dividing n_cells = %d, and a finite dz > 0", nc);
+    st = sed_alloc(ctx);
+    if (st != SDM_OK)
+        return st;
+    cudaStream_t s = ctx->stream;
+    const double *dz_arr = z;
+    void *stage = nullptr;
+    const size_t bz = sizeof(double) * ctx->n_sd;
+    if (!on_device) {
+        stage = ctx->mem.get(bz);
+        if (!stage)
+            return fail(&ctx->error, SDM_ENOMEM, "staging allocation failed");
+        CTX_CUDA(ctx, cudaMemcpyAsync(stage, z, bz, cudaMemcpyHostToDevice, s));
+        dz_arr = (const double *)stage;
+    }
+    uint32_t *d_flags = ctx->sed->flags;
+    unsigned long long *d_bad = (unsigned long long *)(d_flags + 2);
+    CTX_CUDA(ctx, cudaMemsetAsync(d_flags, 0, sizeof(uint32_t), s));
+    CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
+    sed_set_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot, dz_arr,
+                                                        nx, dz, ctx->d_zeta, d_flags, d_bad);
+    uint32_t flags = 0;
+    unsigned long long bad = 0;
+    CTX_CUDA(ctx, cudaGetLastError());
+    CTX_CUDA(ctx, cudaMemcpyAsync(&flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->mem.put(stage, bz);
+    if (flags & 1u) {
+        ctx->has_positions = false;
+        return fail(&ctx->error, SDM_EINVAL, "SD %llu: z must lie in its cell's level [iz dz, (iz + 1) dz)", bad);
+    }
+    ctx->nx = nx;
+    ctx->dz = dz;
+    ctx->has_positions = true;
+    return SDM_OK;
+}
+
+extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes || !ctx->has_positions)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_positions has not been called for the current attributes");
+    SedBuffers &b = *ctx->sed;
+    cudaStream_t s = ctx->stream;
+    const int32_t nc = ctx->cfg.n_cells, n_groups = nc + 1;
+    const int64_t n = ctx->n_sd;
+    CTX_CUDA(ctx, cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * n_groups, s));
+    sed_move_kernel<<<sed_grid(n_groups), kSedNT, 0, s>>>(ctx->d_inst, nc, ctx->n_slots, ctx->nx, ctx->dz,
+                                                           (float)ctx->cfg.dt, ctx->d_zeta, ctx->d_id_of_slot, b.keys[0],
+                                                           b.vals[0], b.zeta_new, b.counts, b.precip);
+    sed_scan_kernel<<<1, 1024, 0, s>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, nc, b.precip + nc);
+    // stable sort of the new groups, SD-id order in
+    const int bits = 32 - __builtin_clz((unsigned)nc | 1u);
+    const int passes = (bits + 7) / 8;
+    const int32_t tiles = (int32_t)((n + kRadixTile - 1) / kRadixTile);
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        radix_hist_kernel<<<tiles, kRadixNT, 0, s>>>(b.keys[cur], n, 8 * p, b.hist, tiles);
+        scan_inplace_kernel<<<1, 1024, 0, s>>>(b.hist, (int64_t)kRadixBuckets * tiles);
+        radix_scatter_kernel<<<tiles, kRadixNT, 0, s>>>(b.keys[cur], b.vals[cur], n, 8 * p, b.hist, tiles,
+                                                         b.keys[cur ^ 1], b.vals[cur ^ 1]);
+        cur ^= 1;
+    }
+    sed_gather_kernel<<<1216, 256, 0, s>>>(n, b.keys[cur], b.vals[cur], b.ustart, b.cell_off2, ctx->d_xi, ctx->d_v,
+                                           b.zeta_new, ctx->d_id_of_slot, b.xi2, b.v2, b.zeta2, b.id2);
+    sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
+                                                           b.id2);
+    CTX_CUDA(ctx, cudaGetLastError());
+    std::vector<int32_t> off(n_groups + 1);
+    double precip = 0.0;
+    CTX_CUDA(ctx, cudaMemcpyAsync(off.data(), b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(&precip, b.precip + nc, sizeof precip, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    // the new layout becomes the state; the old one the next scratch
+    std::swap(ctx->d_xi, b.xi2);
+    std::swap(ctx->d_v, b.v2);
+    std::swap(ctx->d_zeta, b.zeta2);
+    std::swap(ctx->d_id_of_slot, b.id2);
+    std::swap(ctx->d_cell_off, b.cell_off2);
+    std::vector<int32_t> cell_off(off.begin(), off.begin() + nc + 1);
+    int32_t largest = 0;
+    for (int32_t c = 0; c < nc; ++c)
+        largest = std::max(largest, cell_off[c + 1] - cell_off[c]);
+    const bool keep_plan = ctx->self_batch && ctx->h_cell_off == cell_off &&
+                           same_tuning(ctx->self_batch->plan.tuning, current_tuning());
+    ctx->h_cell_off = cell_off;
+    ctx->n_slots = off[n_groups];
+    ctx->largest_cell = largest;
+    ctx->layout_version += 1;
+    ctx->dev_base = ctx->step;
+    InstDev inst = make_inst(ctx);
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
+    if (ctx->self_batch && keep_plan)
+        ctx->self_batch->versions[0] = ctx->layout_version;
+    if (ctx->self_batch && !keep_plan) {
+        batch_release(ctx->self_batch);
+        delete ctx->self_batch;
+        ctx->self_batch = nullptr;
+    }
+    if (precipitated)
+        *precipitated = precip;
+    return SDM_OK;
+}
+
+extern "C" sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, int on_device)
+{
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "sdm_set_attributes has not been called");
+    if (z && !ctx->has_positions)
+        return fail(&ctx->error, SDM_ESTATE, "no positions: sdm_set_positions has not been called");
+    if (!z && !cell)
+        return SDM_OK;
+    cudaStream_t s = ctx->stream;
+    const int32_t nc = ctx->cfg.n_cells;
+    const int32_t nx = ctx->has_positions ? ctx->nx : 1;
+    const int64_t n = ctx->n_sd;
+    if (on_device) {
+        sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
+                                                            ctx->d_zeta, nx, ctx->dz, z, cell);
+        CTX_CUDA(ctx, cudaGetLastError());
+        return SDM_OK;
+    }
+    const size_t bz = sizeof(double) * n, bc = sizeof(int32_t) * n;
+    char *tmp = (char *)ctx->mem.get(bz + bc);
+    if (!tmp)
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
+                                                        ctx->d_zeta, nx, ctx->dz, z ? (double *)tmp : nullptr,
+                                                        cell ? (int32_t *)(tmp + bz) : nullptr);
+    CTX_CUDA(ctx, cudaGetLastError());
+    if (z)
+        CTX_CUDA(ctx, cudaMemcpyAsync(z, tmp, bz, cudaMemcpyDeviceToHost, s));
+    if (cell)
+        CTX_CUDA(ctx, cudaMemcpyAsync(cell, tmp + bz, bc, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->mem.put(tmp, bz + bc);
+    return check_device_status(ctx);
+}

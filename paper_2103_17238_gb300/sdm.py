@@ -30,6 +30,7 @@ EXPORTS = [
     "sdm_get_attributes", "sdm_get_info", "sdm_footprint_bytes", "sdm_destroy", "sdm_last_error",
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
     "sdm_cell_step_noalloc", "sdm_set_tuning", "sdm_get_tuning",
+    "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions",
 ]
 NOALLOC_MAX_SD = 1 << 20
 
@@ -122,11 +123,14 @@ def load(path: str = LIB_PATH):
         L.sdm_batch_last_error.restype = ctypes.c_char_p
         L.sdm_cell_step_noalloc.argtypes = [P(sdm_config), i64, vp, vp, i64, vp]
         L.sdm_set_tuning.argtypes = [P(sdm_tuning)]
+        L.sdm_set_positions.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.c_int]
+        L.sdm_sedimentation_step.argtypes = [vp, P(ctypes.c_double)]
+        L.sdm_get_positions.argtypes = [vp, vp, vp, ctypes.c_int]
         L.sdm_get_tuning.argtypes = [P(sdm_tuning)]
         for name in ("sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
                      "sdm_get_attributes", "sdm_get_info", "sdm_destroy", "sdm_batch_create",
                      "sdm_batch_step", "sdm_batch_destroy", "sdm_cell_step_noalloc", "sdm_set_tuning",
-                     "sdm_get_tuning"):
+                     "sdm_get_tuning", "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -298,6 +302,35 @@ def sdm_cell_step_noalloc(cfg: sdm_config, step: int, xi, volume, stream: int):
                                         ctypes.c_void_p(stream)), "sdm_cell_step_noalloc")
 
 
+def sdm_set_positions(ctx, z, nx: int, dz: float):
+    pz, dev, kz = _ptr_and_flag(z, np.float64)
+    _check(load().sdm_set_positions(ctx, pz, int(nx), float(dz), dev), "sdm_set_positions", ctx)
+
+
+def sdm_sedimentation_step(ctx) -> float:
+    """One sedimentation step; returns the precipitated volume sum(xi v), m^3."""
+    out = ctypes.c_double(0.0)
+    _check(load().sdm_sedimentation_step(ctx, ctypes.byref(out)), "sdm_sedimentation_step", ctx)
+    return out.value
+
+
+def sdm_get_positions(ctx, n_sd: int | None = None, z=None, cell=None, want_z: bool = True):
+    """Heights above the domain bottom and cells (-1: outside) in SD-id order
+    (numpy, or into given tensors)."""
+    if z is None and cell is None:
+        n = int(n_sd if n_sd is not None else sdm_get_info(ctx).n_sd)
+        zz = np.zeros(n, dtype=np.float64) if want_z else None
+        cc = np.zeros(n, dtype=np.int32)
+        _check(load().sdm_get_positions(ctx, zz.ctypes.data if want_z else None, cc.ctypes.data, 0),
+               "sdm_get_positions", ctx)
+        return zz, cc
+    pz, dz_, _ = _ptr_and_flag(z, np.float64) if z is not None else (None, None, None)
+    pc, dc, _ = _ptr_and_flag(cell, np.int32) if cell is not None else (None, None, None)
+    on = dz_ if dz_ is not None else dc
+    _check(load().sdm_get_positions(ctx, pz, pc, on), "sdm_get_positions", ctx)
+    return z, cell
+
+
 def sdm_set_tuning(tuning=None):
     """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block; None: defaults."""
     if tuning is None:
@@ -357,6 +390,17 @@ class Run:
 
     def attributes(self):
         return sdm_get_attributes(self.h)
+
+    def set_positions(self, z, nx: int, dz: float):
+        sdm_set_positions(self.h, z, nx, dz)
+        return self
+
+    def sediment(self) -> float:
+        """One sedimentation step; returns the precipitated volume, m^3."""
+        return sdm_sedimentation_step(self.h)
+
+    def positions(self, want_z: bool = True):
+        return sdm_get_positions(self.h, want_z=want_z)
 
     def info(self) -> sdm_info:
         return sdm_get_info(self.h)
