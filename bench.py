@@ -264,6 +264,7 @@ def run_ours(args, rank: int, world: int):
         extras["large_cells"] = measure_large_cells(sdm, torch)
         extras["kfp32"] = measure_kfp32(sdm, torch, g)
         extras["serving"] = measure_serving(torch, args.serve_requests)
+        extras["sedimentation"] = measure_sedimentation(sdm, torch, g)
     res = None
     if rank == 0:
         res = {
@@ -412,6 +413,49 @@ def measure_large_cells(sdm, torch, steps=10, members=32):
         r.close()
     return {"workload": "32 x Golovin box n_sd=2^20 (one cell each), FP64; state 540 MB > L2",
             "pair_updates_per_s": pairs * steps / dt, "ms_per_step": dt / steps * 1e3}
+
+
+def measure_sedimentation(sdm, torch, g, steps=50):
+    """The grid as 128 columns x 128 levels of 10 m, dt = 1 s: a
+    sedimentation step (fall, regroup, new layout) then a coalescence step.
+    Device times by CUDA events; the coupled step's wall time includes the
+    host's read of the new cell offsets and the launch plan it rebuilds.
+    Algorithmic bytes of the sedimentation step: the whole layout read and
+    written once (xi, v, zeta, id: 28 B per SD each way)."""
+    nx, dz = 128, 10.0
+    rng = np.random.default_rng(12)
+    z = (g.cell // nx).astype(np.float64) * dz + rng.uniform(0.0, dz, g.n_sd)
+    run = sdm.Run(sdm.make_config("geometric", dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+    run.set_attributes(g.xi, g.v, g.cell).set_positions(z, nx, dz)
+    _, cell0 = run.positions(want_z=False)
+    for _ in range(3):
+        run.sediment()
+        run.step(1)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    precip = 0.0
+    t0 = time.perf_counter()
+    for e in ev:
+        e[0].record()
+        precip += run.sediment()
+        e[1].record()
+        e[2].record()
+        run.step(1)
+        e[3].record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / steps
+    sed_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    coal_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    _, cell1 = run.positions(want_z=False)
+    moved = float(np.mean(cell1 != cell0))
+    run.close()
+    gbs = 56.0 * g.n_sd / (sed_ms * 1e-3) / 1e9
+    return {"workload": "grid_geometric 4,194,304 SDs as 128 columns x 128 levels of 10 m, dt = 1 s, heights "
+                        "uniform in each level (rng 12); sedimentation then coalescence per step",
+            "steps": steps, "sedimentation_ms": sed_ms, "coalescence_ms": coal_ms,
+            "coupled_wall_ms": wall * 1e3, "sedimentation_algorithmic_gbs": gbs,
+            "sedimentation_frac_of_measured_hbm": gbs / measured_peaks()[0],
+            "sds_changed_cell_over_run": moved, "precipitated_m3": precip}
 
 
 def measure_kfp32(sdm, torch, g, steps=600):

@@ -9,14 +9,16 @@
 // the bottom of the SD's cell, so a step needs no division.
 //
 // One step on the device:
-//   sed_move_kernel      warp per group (each cell, then the SDs outside the
-//                        domain): the fall, the new group of every SD as a
-//                        key in SD-id order, counts per new group, the water
-//                        that leaves through the bottom per cell;
+//   sed_move_kernel      per slot (four per thread): the fall, the new group
+//                        of every SD (the cells, then n_cells for outside the
+//                        domain) as a key in SD-id order, counts per new
+//                        group, the water that leaves through the bottom;
 //   sed_scan_kernel      new group offsets (unpadded and padded to even
 //                        slots) and the precipitated total, in fixed order;
-//   radix_*_kernel       stable LSD radix sort of the keys (SD-id order in,
-//                        so equal groups keep increasing id);
+//   radix_*_kernel       stable LSD radix sort of the keys, 8-bit digits
+//                        (SD-id order in, so equal groups keep increasing
+//                        id): per-tile digit counts, a scan of each digit's
+//                        row, a scan of the digit totals, a ranked scatter;
 //   sed_gather_kernel    the new layout, gathered from the old one;
 //   sed_pad_kernel       its padding slots.
 // The two layouts swap; the host reads the new offsets for the launch plan.
@@ -35,11 +37,12 @@ constexpr int kRadixBuckets = 256;                  // 8-bit digits
 // ------------------------------------------------------------------ kernels
 // zeta of every slot from z (SD-id order): z - (c / nx) dz, which must lie
 // in [0, dz); flags bit 0 and the first bad id on failure.  SDs outside the
-// domain and padding slots get zeta 0.
+// domain and padding slots get zeta 0.  group[slot] = the slot's group.
 __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restrict__ cell_off, int32_t n_cells,
                                                          int64_t n_slots, const int32_t *__restrict__ id_of_slot,
                                                          const double *__restrict__ z, int32_t nx, double dz,
-                                                         double *__restrict__ zeta, uint32_t *__restrict__ flags,
+                                                         double *__restrict__ zeta, int32_t *__restrict__ group,
+                                                         uint32_t *__restrict__ flags,
                                                          unsigned long long *__restrict__ bad)
 {
     const int lane = threadIdx.x & 31;
@@ -59,6 +62,7 @@ __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restri
                 }
             }
             zeta[s] = zt;
+            group[s] = g;
         }
     }
 }
@@ -86,45 +90,61 @@ __global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restri
     }
 }
 
-// The fall of every SD.  key[id] = its new group (n_cells: outside),
-// val[id] = its slot, zeta_new[slot] = its new height; counts[new group]
-// (one atomic per run of equal groups in a warp's 32 slots); precip[c] =
-// sum of xi v of the SDs of cell c that fell through the bottom (slot order
-// per lane, then a fixed tree over lanes).
+// The fall of every SD, four slots per thread (grid-stride, all loads
+// issued before use).  key[id] = its new group (n_cells: outside), val[id]
+// = its slot, zeta_new[slot] = its new height; counts[new group] (one
+// atomic per run of equal groups among a warp's 32 consecutive slots);
+// precip_part[block] = sum of xi v of the SDs that fell through the bottom
+// (thread order fixed, then a fixed tree over the block).
+constexpr int kSedU = 4;
+constexpr int kSedMaxBlocks = 4096;
+
 __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restrict__ P, int32_t n_cells, int64_t n_slots,
                                                           int32_t nx, double dz, float dt32,
                                                           const double *__restrict__ zeta,
+                                                          const int32_t *__restrict__ group,
                                                           const int32_t *__restrict__ id_of_slot,
                                                           uint32_t *__restrict__ key, uint32_t *__restrict__ val,
                                                           double *__restrict__ zeta_new, uint32_t *__restrict__ counts,
-                                                          double *__restrict__ precip)
+                                                          double *__restrict__ precip_part)
 {
     constexpr unsigned FULL = 0xFFFFFFFFu;
+    __shared__ double s_pr[kSedNT / 32];
     const PairConsts C = pair_consts(P);
     const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const int64_t *__restrict__ gxi = P->xi;
     const double *__restrict__ gv = P->v;
-    for (int g = gw; g <= n_cells; g += nw) {
-        const int64_t lo = P->cell_off[g], hi = g < n_cells ? P->cell_off[g + 1] : n_slots;
-        const bool inside = g < n_cells;
-        const int32_t iz0 = inside ? g / nx : 0, ix = inside ? g % nx : 0;
-        double pr = 0.0;
-        for (int64_t s0 = lo; s0 < hi; s0 += 32) { // warp-uniform trip count
-            const int64_t s = s0 + lane;
-            const int32_t id = s < hi ? id_of_slot[s] : -1;
-            int32_t ng = -1; // -1: padding, nothing to count
-            if (id >= 0) {
-                const int64_t x = gxi[s];
+    const int64_t stride = (int64_t)gridDim.x * kSedNT;
+    double pr = 0.0;
+    // warp-uniform trip count: every lane runs every round (shuffles, ballots)
+    for (int64_t w0 = ((int64_t)blockIdx.x * kSedNT + (threadIdx.x & ~31)); w0 < n_slots; w0 += kSedU * stride) {
+        int32_t id[kSedU], g[kSedU];
+        int64_t x[kSedU];
+        double vv[kSedU], zt[kSedU];
+#pragma unroll
+        for (int u = 0; u < kSedU; ++u) {
+            const int64_t sl = w0 + u * stride + lane;
+            const bool in = sl < n_slots;
+            id[u] = in ? id_of_slot[sl] : -1;
+            g[u] = in ? group[sl] : 0;
+            x[u] = in ? gxi[sl] : 0;
+            vv[u] = in ? gv[sl] : 1.0;
+            zt[u] = in ? zeta[sl] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSedU; ++u) {
+            const int64_t sl = w0 + u * stride + lane;
+            int32_t ng = -1; // -1: no SD in this slot
+            if (id[u] >= 0) {
                 double zn = 0.0;
                 ng = n_cells;
-                if (inside && x > 0) {
-                    const double vv = gv[s];
+                if (g[u] < n_cells && x[u] > 0) {
                     bool in_range;
-                    const float vf = d2f_rn(vv, in_range);
+                    const float vf = d2f_rn(vv[u], in_range);
                     const double d = (double)__fmul_rn(vt32c(C, radius32(vf)), dt32);
-                    double zz = __dsub_rn(zeta[s], d);
-                    int32_t iz = iz0;
+                    double zz = __dsub_rn(zt[u], d);
+                    int32_t iz = g[u] / nx;
+                    const int32_t ix = g[u] - iz * nx;
                     while (zz < 0.0) { // at most as many levels as the SD falls through
                         iz -= 1;
                         if (iz < 0)
@@ -132,7 +152,7 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
                         zz = __dadd_rn(zz, dz);
                     }
                     if (iz < 0) {
-                        pr = __dadd_rn(pr, __dmul_rn(xi2d(x), vv));
+                        pr = __dadd_rn(pr, __dmul_rn(xi2d(x[u]), vv[u]));
                     } else {
                         if (zz >= dz) { // zeta + dz rounded up to dz: on the boundary, level above
                             iz += 1;
@@ -142,9 +162,9 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
                         zn = zz;
                     }
                 }
-                key[id] = (uint32_t)ng;
-                val[id] = (uint32_t)s;
-                zeta_new[s] = zn;
+                key[id[u]] = (uint32_t)ng;
+                val[id[u]] = (uint32_t)sl;
+                zeta_new[sl] = zn;
             }
             const int32_t nxt = __shfl_down_sync(FULL, ng, 1);
             const bool end = lane == 31 || nxt != ng;
@@ -155,20 +175,27 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
                 atomicAdd(&counts[ng], (uint32_t)(lane - start + 1));
             }
         }
+    }
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1)
-            pr = __dadd_rn(pr, __shfl_down_sync(FULL, pr, d));
-        if (lane == 0 && inside)
-            precip[g] = pr;
+    for (int d = 16; d > 0; d >>= 1)
+        pr = __dadd_rn(pr, __shfl_down_sync(FULL, pr, d));
+    if (lane == 0)
+        s_pr[threadIdx.x >> 5] = pr;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kSedNT / 32; ++w)
+            t = __dadd_rn(t, s_pr[w]);
+        precip_part[blockIdx.x] = t;
     }
 }
 
 // One block: ustart = exclusive scan of counts[0 .. n_groups) (total at
 // ustart[n_groups]); poff the same with every count rounded up to even;
-// *precip_total = sum of precip[0 .. n_cells) in a fixed order.
+// *precip_total = sum of precip[0 .. n_parts) in a fixed order.
 __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restrict__ counts, int32_t n_groups,
                                                         int32_t *__restrict__ ustart, int32_t *__restrict__ poff,
-                                                        const double *__restrict__ precip, int32_t n_cells,
+                                                        const double *__restrict__ precip, int32_t n_parts,
                                                         double *__restrict__ precip_total)
 {
     __shared__ uint32_t s_u[1024], s_p[1024];
@@ -198,8 +225,8 @@ __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restri
         ustart[n_groups] = (int32_t)tu;
         poff[n_groups] = (int32_t)tp;
     }
-    const int pper = (n_cells + 1023) / 1024;
-    const int pa = min(n_cells, t * pper), pb = min(n_cells, pa + pper);
+    const int pper = (n_parts + 1023) / 1024;
+    const int pa = min(n_parts, t * pper), pb = min(n_parts, pa + pper);
     double pr = 0.0;
     for (int c = pa; c < pb; ++c)
         pr = __dadd_rn(pr, precip[c]);
@@ -237,26 +264,40 @@ __global__ void __launch_bounds__(kRadixNT) radix_hist_kernel(const uint32_t *__
     hist[(int64_t)t * n_tiles + blockIdx.x] = h[t];
 }
 
-// One block: exclusive scan of a[0 .. n) in place.
-__global__ void __launch_bounds__(1024) scan_inplace_kernel(uint32_t *__restrict__ a, int64_t n)
+// Block d: exclusive scan, in place, of the counts of digit d over the
+// tiles (one contiguous row of hist), in chunks of 1024 with a running
+// carry; total[d] = the row's sum.
+__global__ void __launch_bounds__(1024) radix_row_scan_kernel(uint32_t *__restrict__ hist, int32_t n_tiles,
+                                                              uint32_t *__restrict__ total)
 {
     __shared__ uint32_t s[1024];
     __shared__ uint32_t s_warp[32];
     const int t = threadIdx.x;
-    const int64_t per = (n + 1023) / 1024;
-    const int64_t lo = min(n, (int64_t)t * per), hi = min(n, lo + per);
-    uint32_t sum = 0;
-    for (int64_t i = lo; i < hi; ++i)
-        sum += a[i];
-    s[t] = sum;
-    __syncthreads();
-    block_exclusive_scan<1024, 1024>(s, s_warp);
-    uint32_t run = s[t];
-    for (int64_t i = lo; i < hi; ++i) {
-        const uint32_t x = a[i];
-        a[i] = run;
-        run += x;
+    uint32_t *row = hist + (int64_t)blockIdx.x * n_tiles;
+    uint32_t carry = 0;
+    for (int32_t c0 = 0; c0 < n_tiles; c0 += 1024) {
+        const int32_t i = c0 + t;
+        s[t] = i < n_tiles ? row[i] : 0u;
+        __syncthreads();
+        const uint32_t sum = block_exclusive_scan<1024, 1024>(s, s_warp);
+        if (i < n_tiles)
+            row[i] = carry + s[t];
+        carry += sum;
+        __syncthreads();
     }
+    if (t == 0)
+        total[blockIdx.x] = carry;
+}
+
+// One block of 256: exclusive scan of the digit totals, in place.
+__global__ void __launch_bounds__(kRadixBuckets) radix_digit_scan_kernel(uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t s[kRadixBuckets];
+    __shared__ uint32_t s_warp[32];
+    s[threadIdx.x] = total[threadIdx.x];
+    __syncthreads();
+    block_exclusive_scan<kRadixBuckets, kRadixBuckets>(s, s_warp);
+    total[threadIdx.x] = s[threadIdx.x];
 }
 
 // Stable scatter of one pass: tile keys in index order (round-major, thread
@@ -265,6 +306,7 @@ __global__ void __launch_bounds__(1024) scan_inplace_kernel(uint32_t *__restrict
 __global__ void __launch_bounds__(kRadixNT) radix_scatter_kernel(const uint32_t *__restrict__ keys_in,
                                                                  const uint32_t *__restrict__ vals_in, int64_t n,
                                                                  int shift, const uint32_t *__restrict__ offs,
+                                                                 const uint32_t *__restrict__ digit_base,
                                                                  int32_t n_tiles, uint32_t *__restrict__ keys_out,
                                                                  uint32_t *__restrict__ vals_out)
 {
@@ -272,7 +314,7 @@ __global__ void __launch_bounds__(kRadixNT) radix_scatter_kernel(const uint32_t 
     __shared__ uint32_t s_base[kRadixBuckets + 1];
     __shared__ uint32_t s_wcnt[NW][kRadixBuckets + 1];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    s_base[t] = offs[(int64_t)t * n_tiles + blockIdx.x];
+    s_base[t] = digit_base[t] + offs[(int64_t)t * n_tiles + blockIdx.x];
     for (int i = t; i < NW * (kRadixBuckets + 1); i += kRadixNT)
         (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
@@ -318,7 +360,7 @@ __global__ void sed_gather_kernel(int64_t n_sd, const uint32_t *__restrict__ key
                                   const int64_t *__restrict__ xi, const double *__restrict__ v,
                                   const double *__restrict__ zeta_new, const int32_t *__restrict__ id_of_slot,
                                   int64_t *__restrict__ xi2, double *__restrict__ v2, double *__restrict__ zeta2,
-                                  int32_t *__restrict__ id2)
+                                  int32_t *__restrict__ id2, int32_t *__restrict__ group2)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_sd; j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t g = keys[j], s = vals[j];
@@ -327,13 +369,14 @@ __global__ void sed_gather_kernel(int64_t n_sd, const uint32_t *__restrict__ key
         v2[p] = v[s];
         zeta2[p] = zeta_new[s];
         id2[p] = id_of_slot[s];
+        group2[p] = (int32_t)g;
     }
 }
 
 // The padding slot after every odd group of the new layout.
 __global__ void sed_pad_kernel(int32_t n_groups, const int32_t *__restrict__ ustart, const int32_t *__restrict__ poff,
                                int64_t *__restrict__ xi2, double *__restrict__ v2, double *__restrict__ zeta2,
-                               int32_t *__restrict__ id2)
+                               int32_t *__restrict__ id2, int32_t *__restrict__ group2)
 {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
         for (int32_t p = poff[g] + (ustart[g + 1] - ustart[g]); p < poff[g + 1]; ++p) {
@@ -341,6 +384,7 @@ __global__ void sed_pad_kernel(int32_t n_groups, const int32_t *__restrict__ ust
             v2[p] = 1.0;
             zeta2[p] = 0.0;
             id2[p] = -1;
+            group2[p] = g;
         }
     }
 }
@@ -353,14 +397,16 @@ struct SedBuffers {
     double *v2 = nullptr;
     double *zeta2 = nullptr;
     int32_t *id2 = nullptr;
+    int32_t *group = nullptr;     // group of every slot of the current layout
+    int32_t *group2 = nullptr;
     int32_t *cell_off2 = nullptr; // n_cells + 2
     double *zeta_new = nullptr;   // per slot of the old layout
     uint32_t *keys[2] = {};
     uint32_t *vals[2] = {};
     uint32_t *counts = nullptr; // n_cells + 1
     int32_t *ustart = nullptr;  // n_cells + 2
-    double *precip = nullptr;   // n_cells + 1 (the last: the total)
-    uint32_t *hist = nullptr;   // 256 x tiles
+    double *precip = nullptr;   // per-block parts of the move kernel, then the total
+    uint32_t *hist = nullptr;   // 256 x tiles, then 256 digit totals
     uint32_t *flags = nullptr;  // flags, then the first bad id (8-byte aligned)
 };
 
@@ -368,8 +414,9 @@ void sed_release(sdm_ctx *ctx)
 {
     if (ctx->sed) {
         SedBuffers &b = *ctx->sed;
-        void *bufs[] = {b.xi2,     b.v2,      b.zeta2,  b.id2,    b.cell_off2, b.zeta_new, b.keys[0], b.keys[1],
-                        b.vals[0], b.vals[1], b.counts, b.ustart, b.precip,    b.hist,     b.flags};
+        void *bufs[] = {b.xi2,      b.v2,       b.zeta2,    b.id2,    b.group,  b.group2,
+                        b.cell_off2, b.zeta_new, b.keys[0], b.keys[1], b.vals[0], b.vals[1],
+                        b.counts,   b.ustart,   b.precip,   b.hist,   b.flags};
         for (void *p : bufs)
             ctx->mem.put(p, 0);
         delete ctx->sed;
@@ -401,6 +448,8 @@ sdm_status sed_alloc(sdm_ctx *ctx)
     b.v2 = sed_get<double>(ctx, slots);
     b.zeta2 = sed_get<double>(ctx, slots);
     b.id2 = sed_get<int32_t>(ctx, slots);
+    b.group = sed_get<int32_t>(ctx, slots);
+    b.group2 = sed_get<int32_t>(ctx, slots);
     b.cell_off2 = sed_get<int32_t>(ctx, (size_t)nc + 2);
     b.zeta_new = sed_get<double>(ctx, slots);
     for (int i = 0; i < 2; ++i) {
@@ -409,17 +458,18 @@ sdm_status sed_alloc(sdm_ctx *ctx)
     }
     b.counts = sed_get<uint32_t>(ctx, (size_t)nc + 1);
     b.ustart = sed_get<int32_t>(ctx, (size_t)nc + 2);
-    b.precip = sed_get<double>(ctx, (size_t)nc + 1);
-    b.hist = sed_get<uint32_t>(ctx, (size_t)kRadixBuckets * tiles + 1);
+    b.precip = sed_get<double>(ctx, (size_t)kSedMaxBlocks + 1);
+    b.hist = sed_get<uint32_t>(ctx, (size_t)kRadixBuckets * tiles + kRadixBuckets);
     b.flags = sed_get<uint32_t>(ctx, 4);
-    const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.cell_off2 && b.zeta_new && b.keys[0] &&
+    const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.group && b.group2 && b.cell_off2 &&
+                    b.zeta_new && b.keys[0] &&
                     b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart && b.precip && b.hist && b.flags;
     if (!ok) {
         sed_release(ctx);
         return fail(&ctx->error, SDM_ENOMEM, "sedimentation buffers: device allocation failed");
     }
-    ctx->device_bytes += slots * (8 + 8 + 8 + 8 + 4 + 8) + cap * 16 + ((int64_t)nc + 2) * 24 +
-                         (int64_t)kRadixBuckets * tiles * 4;
+    ctx->device_bytes += slots * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 8) + cap * 16 + ((int64_t)nc + 2) * 16 +
+                         (int64_t)kRadixBuckets * (tiles + 1) * 4;
     return SDM_OK;
 }
 
@@ -459,7 +509,7 @@ extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t n
     CTX_CUDA(ctx, cudaMemsetAsync(d_flags, 0, sizeof(uint32_t), s));
     CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
     sed_set_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot, dz_arr,
-                                                        nx, dz, ctx->d_zeta, d_flags, d_bad);
+                                                        nx, dz, ctx->d_zeta, ctx->sed->group, d_flags, d_bad);
     uint32_t flags = 0;
     unsigned long long bad = 0;
     CTX_CUDA(ctx, cudaGetLastError());
@@ -489,31 +539,36 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     const int32_t nc = ctx->cfg.n_cells, n_groups = nc + 1;
     const int64_t n = ctx->n_sd;
     CTX_CUDA(ctx, cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * n_groups, s));
-    sed_move_kernel<<<sed_grid(n_groups), kSedNT, 0, s>>>(ctx->d_inst, nc, ctx->n_slots, ctx->nx, ctx->dz,
-                                                           (float)ctx->cfg.dt, ctx->d_zeta, ctx->d_id_of_slot, b.keys[0],
-                                                           b.vals[0], b.zeta_new, b.counts, b.precip);
-    sed_scan_kernel<<<1, 1024, 0, s>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, nc, b.precip + nc);
+    const int move_blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>(kSedMaxBlocks, (ctx->n_slots + (int64_t)kSedNT * kSedU - 1) / ((int64_t)kSedNT * kSedU)));
+    sed_move_kernel<<<move_blocks, kSedNT, 0, s>>>(ctx->d_inst, nc, ctx->n_slots, ctx->nx, ctx->dz, (float)ctx->cfg.dt,
+                                                   ctx->d_zeta, b.group, ctx->d_id_of_slot, b.keys[0], b.vals[0],
+                                                   b.zeta_new, b.counts, b.precip);
+    sed_scan_kernel<<<1, 1024, 0, s>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, move_blocks,
+                                       b.precip + kSedMaxBlocks);
     // stable sort of the new groups, SD-id order in
     const int bits = 32 - __builtin_clz((unsigned)nc | 1u);
     const int passes = (bits + 7) / 8;
     const int32_t tiles = (int32_t)((n + kRadixTile - 1) / kRadixTile);
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
+        uint32_t *digit_total = b.hist + (size_t)kRadixBuckets * tiles;
         radix_hist_kernel<<<tiles, kRadixNT, 0, s>>>(b.keys[cur], n, 8 * p, b.hist, tiles);
-        scan_inplace_kernel<<<1, 1024, 0, s>>>(b.hist, (int64_t)kRadixBuckets * tiles);
-        radix_scatter_kernel<<<tiles, kRadixNT, 0, s>>>(b.keys[cur], b.vals[cur], n, 8 * p, b.hist, tiles,
-                                                         b.keys[cur ^ 1], b.vals[cur ^ 1]);
+        radix_row_scan_kernel<<<kRadixBuckets, 1024, 0, s>>>(b.hist, tiles, digit_total);
+        radix_digit_scan_kernel<<<1, kRadixBuckets, 0, s>>>(digit_total);
+        radix_scatter_kernel<<<tiles, kRadixNT, 0, s>>>(b.keys[cur], b.vals[cur], n, 8 * p, b.hist, digit_total,
+                                                         tiles, b.keys[cur ^ 1], b.vals[cur ^ 1]);
         cur ^= 1;
     }
     sed_gather_kernel<<<1216, 256, 0, s>>>(n, b.keys[cur], b.vals[cur], b.ustart, b.cell_off2, ctx->d_xi, ctx->d_v,
-                                           b.zeta_new, ctx->d_id_of_slot, b.xi2, b.v2, b.zeta2, b.id2);
+                                           b.zeta_new, ctx->d_id_of_slot, b.xi2, b.v2, b.zeta2, b.id2, b.group2);
     sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
-                                                           b.id2);
+                                                           b.id2, b.group2);
     CTX_CUDA(ctx, cudaGetLastError());
     std::vector<int32_t> off(n_groups + 1);
     double precip = 0.0;
     CTX_CUDA(ctx, cudaMemcpyAsync(off.data(), b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(&precip, b.precip + nc, sizeof precip, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(&precip, b.precip + kSedMaxBlocks, sizeof precip, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
     // the new layout becomes the state; the old one the next scratch
     std::swap(ctx->d_xi, b.xi2);
@@ -521,6 +576,7 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     std::swap(ctx->d_zeta, b.zeta2);
     std::swap(ctx->d_id_of_slot, b.id2);
     std::swap(ctx->d_cell_off, b.cell_off2);
+    std::swap(b.group, b.group2);
     std::vector<int32_t> cell_off(off.begin(), off.begin() + nc + 1);
     int32_t largest = 0;
     for (int32_t c = 0; c < nc; ++c)
