@@ -52,6 +52,7 @@ WORKLOAD = ("grid_geometric: 128x128 cells x 256 SDs (4,194,304 SDs), dV=1e3 m^3
 KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
+EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "serving", "sedimentation")
 
 
 def kernel_source_hash() -> str:
@@ -259,12 +260,18 @@ def run_ours(args, rank: int, world: int):
     e2e = measure_e2e(args, g, sdm, torch, pairs0)
     run.close()
     extras = {}
-    if rank == 0 and not args.no_extras:
-        extras["batched_vs_plain"] = measure_batched_vs_plain(sdm, torch)
-        extras["large_cells"] = measure_large_cells(sdm, torch)
-        extras["kfp32"] = measure_kfp32(sdm, torch, g)
-        extras["serving"] = measure_serving(torch, args.serve_requests)
-        extras["sedimentation"] = measure_sedimentation(sdm, torch, g)
+    wanted = set() if args.no_extras else set(EXTRAS if args.extras == "all" else args.extras.split(","))
+    if rank == 0:
+        if "batched_vs_plain" in wanted:
+            extras["batched_vs_plain"] = measure_batched_vs_plain(sdm, torch)
+        if "large_cells" in wanted:
+            extras["large_cells"] = measure_large_cells(sdm, torch)
+        if "kfp32" in wanted:
+            extras["kfp32"] = measure_kfp32(sdm, torch, g)
+        if "serving" in wanted:
+            extras["serving"] = measure_serving(torch, args.serve_requests)
+        if "sedimentation" in wanted:
+            extras["sedimentation"] = measure_sedimentation(sdm, torch, g)
     res = None
     if rank == 0:
         res = {
@@ -558,7 +565,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched / serving / KFP32 / large-cell lines")
+    ap.add_argument("--no-extras", action="store_true", help="skip every extra line (same as --extras none)")
+    ap.add_argument("--extras", default="all",
+                    help="comma-separated extra lines to measure: " + ",".join(EXTRAS) + " (default all)")
     ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
