@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restri
             const int32_t id = id_of_slot[s];
             double zt = 0.0;
             if (id >= 0 && g < n_cells) {
-                zt = __dsub_rn(z[id], base);
+                // + 0 turns a -0 height into +0 (the fall tests signs bitwise)
+                zt = __dadd_rn(__dsub_rn(z[id], base), 0.0);
                 if (!(zt >= 0.0 && zt < dz)) {
                     atomicOr(flags, 1u);
                     atomicMin(bad, (unsigned long long)id);
@@ -99,6 +100,28 @@ __global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restri
 constexpr int kSedU = 4;
 constexpr int kSedMaxBlocks = 4096;
 
+// The binary64 value of a binary32, exactly, on the integer pipe for normal
+// numbers (zero, subnormals and non-finite values by the conversion).
+__device__ __forceinline__ double f2d_exact(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu)
+        return (double)f;
+    return __longlong_as_double((long long)(((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                                            ((uint64_t)(b & 0x7FFFFFu) << 29)));
+}
+
+// x < 0 for the heights of this step (never -0: they start >= +0, and
+// x - x and x + y round to +0) by the sign bit, on the integer pipe.
+__device__ __forceinline__ bool dneg(double x) { return __double2hiint(x) < 0; }
+
+// x >= y for non-negative binary64 values: their bit patterns order alike.
+__device__ __forceinline__ bool dge_pos(double x, double y)
+{
+    return __double_as_longlong(x) >= __double_as_longlong(y);
+}
+
 __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restrict__ P, int32_t n_cells, int64_t n_slots,
                                                           int32_t nx, double dz, float dt32,
                                                           const double *__restrict__ zeta,
@@ -141,24 +164,25 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
                 if (g[u] < n_cells && x[u] > 0) {
                     bool in_range;
                     const float vf = d2f_rn(vv[u], in_range);
-                    const double d = (double)__fmul_rn(vt32c(C, radius32(vf)), dt32);
+                    const double d = f2d_exact(__fmul_rn(vt32c(C, radius32(vf)), dt32));
                     double zz = __dsub_rn(zt[u], d);
-                    int32_t iz = g[u] / nx;
-                    const int32_t ix = g[u] - iz * nx;
-                    while (zz < 0.0) { // at most as many levels as the SD falls through
-                        iz -= 1;
-                        if (iz < 0)
+                    // crossing k levels takes cell c to c - k nx; below level 0
+                    // exactly when that is negative (0 <= column < nx)
+                    int32_t c = g[u];
+                    while (dneg(zz)) { // at most as many levels as the SD falls through
+                        c -= nx;
+                        if (c < 0)
                             break;
                         zz = __dadd_rn(zz, dz);
                     }
-                    if (iz < 0) {
+                    if (c < 0) {
                         pr = __dadd_rn(pr, __dmul_rn(xi2d(x[u]), vv[u]));
                     } else {
-                        if (zz >= dz) { // zeta + dz rounded up to dz: on the boundary, level above
-                            iz += 1;
+                        if (dge_pos(zz, dz)) { // zeta + dz rounded up to dz: on the boundary, level above
+                            c += nx;
                             zz = 0.0;
                         }
-                        ng = iz * nx + ix;
+                        ng = c;
                         zn = zz;
                     }
                 }

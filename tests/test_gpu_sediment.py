@@ -47,6 +47,8 @@ def _column_state(rng, nx, nz, dz, max_per_cell=300):
     # inside its level (the sum can round up to the level's top)
     top = (cell // nx + 1).astype(np.float64) * dz
     z = np.where((cell >= 0) & (z >= top), np.nextafter(top, 0.0), z)
+    lvl0 = np.nonzero((cell >= 0) & (cell < nx))[0][:3]
+    z[lvl0] = -0.0  # a signed zero at the domain bottom
     perm = rng.permutation(n)
     return xi[perm], v[perm], cell[perm], z[perm]
 
