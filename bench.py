@@ -55,13 +55,15 @@ L2_FLUSH_BYTES = 256 << 20
 EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "serving", "sedimentation")
 
 
+KERNEL_SOURCES = ("sdm_device.cuh", "sdm_kernels.cuh")  # the step kernel and every helper it uses
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_17238_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

@@ -246,7 +246,7 @@ sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, int on_devi
  * and sets the fastest. */
 typedef struct sdm_tuning {
     int32_t smem_max_sd;     /* largest cell sorted in shared memory: 512, 1024, 2048 or 4096 (default) */
-    int32_t warp_cell_max;   /* largest cell run by one warp: 0, 64, 128 or 256 (default), <= smem_max_sd */
+    int32_t warp_cell_max;   /* largest cell run by one warp: 0, 64, 128, 256 or 512 (default), <= smem_max_sd */
     int32_t warps_per_block; /* warps per block of the warp-per-cell kernel: 1, 2 (default) or 4 */
     int32_t reserved0;       /* must be 0 */
 } sdm_tuning;

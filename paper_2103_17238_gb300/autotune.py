@@ -24,7 +24,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sdm_gb300", "au
 CANDIDATES = [
     dict(smem_max_sd=s, warp_cell_max=w, warps_per_block=k)
     for s in (1024, 2048, 4096)
-    for w in (0, 128, 256)
+    for w in (0, 128, 256, 512)
     for k in ((2,) if w == 0 else (1, 2, 4))
 ]
 

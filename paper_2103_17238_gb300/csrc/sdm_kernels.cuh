@@ -419,8 +419,8 @@ __device__ __forceinline__ void cmp_swap(uint32_t &a, uint32_t &b)
     a = lo;
 }
 
-// Sorts E = 2, 4 or 8 words held in registers (Batcher's odd-even merge
-// networks: 1, 5 and 19 comparators).
+// Sorts E = 2, 4, 8 or 16 words held in registers (Batcher's odd-even merge
+// networks: 1, 5, 19 and 63 comparators).
 template <int E>
 __device__ __forceinline__ void sort_net(uint32_t (&v)[E])
 {
@@ -432,8 +432,72 @@ __device__ __forceinline__ void sort_net(uint32_t (&v)[E])
         cmp_swap(v[0], v[2]);
         cmp_swap(v[1], v[3]);
         cmp_swap(v[1], v[2]);
+    } else if constexpr (E == 16) {
+        cmp_swap(v[0], v[1]);
+        cmp_swap(v[2], v[3]);
+        cmp_swap(v[0], v[2]);
+        cmp_swap(v[1], v[3]);
+        cmp_swap(v[1], v[2]);
+        cmp_swap(v[4], v[5]);
+        cmp_swap(v[6], v[7]);
+        cmp_swap(v[4], v[6]);
+        cmp_swap(v[5], v[7]);
+        cmp_swap(v[5], v[6]);
+        cmp_swap(v[0], v[4]);
+        cmp_swap(v[2], v[6]);
+        cmp_swap(v[2], v[4]);
+        cmp_swap(v[1], v[5]);
+        cmp_swap(v[3], v[7]);
+        cmp_swap(v[3], v[5]);
+        cmp_swap(v[1], v[2]);
+        cmp_swap(v[3], v[4]);
+        cmp_swap(v[5], v[6]);
+        cmp_swap(v[8], v[9]);
+        cmp_swap(v[10], v[11]);
+        cmp_swap(v[8], v[10]);
+        cmp_swap(v[9], v[11]);
+        cmp_swap(v[9], v[10]);
+        cmp_swap(v[12], v[13]);
+        cmp_swap(v[14], v[15]);
+        cmp_swap(v[12], v[14]);
+        cmp_swap(v[13], v[15]);
+        cmp_swap(v[13], v[14]);
+        cmp_swap(v[8], v[12]);
+        cmp_swap(v[10], v[14]);
+        cmp_swap(v[10], v[12]);
+        cmp_swap(v[9], v[13]);
+        cmp_swap(v[11], v[15]);
+        cmp_swap(v[11], v[13]);
+        cmp_swap(v[9], v[10]);
+        cmp_swap(v[11], v[12]);
+        cmp_swap(v[13], v[14]);
+        cmp_swap(v[0], v[8]);
+        cmp_swap(v[4], v[12]);
+        cmp_swap(v[4], v[8]);
+        cmp_swap(v[2], v[10]);
+        cmp_swap(v[6], v[14]);
+        cmp_swap(v[6], v[10]);
+        cmp_swap(v[2], v[4]);
+        cmp_swap(v[6], v[8]);
+        cmp_swap(v[10], v[12]);
+        cmp_swap(v[1], v[9]);
+        cmp_swap(v[5], v[13]);
+        cmp_swap(v[5], v[9]);
+        cmp_swap(v[3], v[11]);
+        cmp_swap(v[7], v[15]);
+        cmp_swap(v[7], v[11]);
+        cmp_swap(v[3], v[5]);
+        cmp_swap(v[7], v[9]);
+        cmp_swap(v[11], v[13]);
+        cmp_swap(v[1], v[2]);
+        cmp_swap(v[3], v[4]);
+        cmp_swap(v[5], v[6]);
+        cmp_swap(v[7], v[8]);
+        cmp_swap(v[9], v[10]);
+        cmp_swap(v[11], v[12]);
+        cmp_swap(v[13], v[14]);
     } else {
-        static_assert(E == 8, "sort_net: 2, 4 or 8 words");
+        static_assert(E == 8, "sort_net: 2, 4, 8 or 16 words");
         cmp_swap(v[0], v[1]);
         cmp_swap(v[2], v[3]);
         cmp_swap(v[4], v[5]);
@@ -462,9 +526,10 @@ constexpr int kMaxSwapRounds = 32;
 
 // Position, among the n words of one bucket, of the SD of rank rk in full
 // (key, rank) order; the keys are drawn again.  Taken only by buckets in
-// which two keys share their top 24 bits (about one cell in 500 at 256 SDs).
+// which two keys share the bits above the rank field (about one cell in 500
+// at 256 SDs, one in 60 at 512).
 __device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cell, int64_t s, const uint32_t *w,
-                                                     uint32_t n, uint32_t rk)
+                                                     uint32_t n, uint32_t rk, uint32_t rank_mask)
 {
     auto full_key = [&](uint32_t r) {
         const uint4 k = draw4(seed, r >> 1, cell, s, 0u);
@@ -473,7 +538,7 @@ __device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cel
     const uint64_t kk = full_key(rk);
     uint32_t c = 0;
     for (uint32_t m = 0; m < n; ++m) {
-        const uint32_t r = w[m] & 255u;
+        const uint32_t r = w[m] & rank_mask;
         c += key_less(full_key(r), r, kk, rk) ? 1u : 0u;
     }
     return c;
@@ -488,8 +553,11 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
     constexpr int LB = ilog2_c(CAP);
     constexpr int RP = CAP / 64 > 0 ? CAP / 64 : 1; // rank pairs per lane
     constexpr int BPL = NB / 32;                   // buckets per lane in the scan
-    static_assert((1 << LB) == CAP && CAP >= 64 && CAP <= 256, "warp kernel: CAP in 64..256");
+    static_assert((1 << LB) == CAP && CAP >= 64 && CAP <= 512, "warp kernel: CAP in 64..512");
     constexpr unsigned FULL = 0xFFFFFFFFu;
+    constexpr int RB = LB > 8 ? LB : 8;      // rank bits of a sort word
+    constexpr uint32_t RM = (1u << RB) - 1u; // rank mask
+    constexpr int KG = RP < 4 ? RP : 4;      // Philox blocks drawn at a time
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -592,29 +660,33 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
         __syncwarp();
 
         // Sort words of live SDs and their bucket slots.  A word holds the
-        // top 24 bits of the SD's 64-bit key and its 8-bit rank, so words
-        // order as (key, rank) except between keys that share those 24 bits;
-        // such keys fall in one bucket and the fixup below orders them by
-        // their full keys.  Every lane draws all its Philox blocks first so
-        // that the independent chains interleave.
-        uint4 kw[RP];
-#pragma unroll
-        for (int r = 0; r < RP; ++r)
-            kw[r] = draw4(seed, (uint32_t)(lane + 32 * r), cell, s, 0u);
+        // top 32 - RB bits of the SD's 64-bit key above its RB-bit rank, so
+        // words order as (key, rank) except between keys that share those
+        // bits; such keys fall in one bucket and the fixup below orders them
+        // by their full keys.  Every lane draws KG Philox blocks at a time so
+        // that independent chains interleave.
         uint32_t word[2 * RP];
         uint32_t slot[2 * RP];
 #pragma unroll
-        for (int r = 0; r < RP; ++r) {
-            const int q = lane + 32 * r;
-            slot[2 * r] = 0xFFFFFFFFu;
-            slot[2 * r + 1] = 0xFFFFFFFFu;
-            word[2 * r] = (kw[r].x & 0xFFFFFF00u) | (uint32_t)(2 * q);
-            word[2 * r + 1] = (kw[r].z & 0xFFFFFF00u) | (uint32_t)(2 * q + 1);
-            if (2 * q < n) {
-                if (xs[2 * q] > 0)
-                    slot[2 * r] = atomicAdd(&s_hist[word[2 * r] >> (32 - LB)], 1u);
-                if (xs[2 * q + 1] > 0)
-                    slot[2 * r + 1] = atomicAdd(&s_hist[word[2 * r + 1] >> (32 - LB)], 1u);
+        for (int r0 = 0; r0 < RP; r0 += KG) {
+            uint4 kw[KG];
+#pragma unroll
+            for (int r = 0; r < KG; ++r)
+                kw[r] = draw4(seed, (uint32_t)(lane + 32 * (r0 + r)), cell, s, 0u);
+#pragma unroll
+            for (int r = 0; r < KG; ++r) {
+                const int q = lane + 32 * (r0 + r);
+                const int i = 2 * (r0 + r);
+                slot[i] = 0xFFFFFFFFu;
+                slot[i + 1] = 0xFFFFFFFFu;
+                word[i] = (kw[r].x & ~RM) | (uint32_t)(2 * q);
+                word[i + 1] = (kw[r].z & ~RM) | (uint32_t)(2 * q + 1);
+                if (2 * q < n) {
+                    if (xs[2 * q] > 0)
+                        slot[i] = atomicAdd(&s_hist[word[i] >> (32 - LB)], 1u);
+                    if (xs[2 * q + 1] > 0)
+                        slot[i + 1] = atomicAdd(&s_hist[word[i + 1] >> (32 - LB)], 1u);
+                }
             }
         }
         __syncwarp();
@@ -653,7 +725,7 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             // can then be out of order only inside buckets that straddle a
             // lane boundary; neighbouring lanes swap inverted boundary words
             // and sort again until no boundary is inverted (every swap
-            // removes an inversion).  Equal 24-bit prefixes end up adjacent;
+            // removes an inversion).  Equal key prefixes end up adjacent;
             // cells holding one take the per-element fixup with full keys.
             constexpr int E = CAP / 32;
             uint32_t v[E];
@@ -697,21 +769,24 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             bool prefix_tie = false;
 #pragma unroll
             for (int i = 0; i + 1 < E; ++i)
-                prefix_tie |= ((v[i] ^ v[i + 1]) < 256u) & (v[i] != v[i + 1]);
+                prefix_tie |= ((v[i] ^ v[i + 1]) <= RM) & (v[i] != v[i + 1]);
             const uint32_t nf = __shfl_down_sync(FULL, v[0], 1);
             if (lane < 31)
-                prefix_tie |= ((v[E - 1] ^ nf) < 256u) & (v[E - 1] != nf);
+                prefix_tie |= ((v[E - 1] ^ nf) <= RM) & (v[E - 1] != nf);
             if (fast && !__any_sync(FULL, prefix_tie)) {
                 uint32_t pk[E / 2];
 #pragma unroll
                 for (int i = 0; i < E / 2; ++i)
-                    pk[i] = (v[2 * i] & 255u) | ((v[2 * i + 1] & 255u) << 16);
+                    pk[i] = (v[2 * i] & RM) | ((v[2 * i + 1] & RM) << 16);
                 if constexpr (E == 2) {
                     reinterpret_cast<uint32_t *>(s_perm)[lane] = pk[0];
                 } else if constexpr (E == 4) {
                     reinterpret_cast<uint2 *>(s_perm)[lane] = make_uint2(pk[0], pk[1]);
                 } else {
-                    reinterpret_cast<uint4 *>(s_perm)[lane] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+                    for (int i = 0; i < E / 8; ++i)
+                        reinterpret_cast<uint4 *>(s_perm)[lane * (E / 8) + i] =
+                            make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
                 }
             } else {
                 for (uint32_t pos = lane; pos < n_c; pos += 32) {
@@ -724,11 +799,11 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                     for (uint32_t m = lo; m < hi; ++m) {
                         const uint32_t wm = s_word[m];
                         c += wm < wv ? 1u : 0u;
-                        tie |= ((wm ^ wv) < 256u) & (wm != wv);
+                        tie |= ((wm ^ wv) <= RM) & (wm != wv);
                     }
                     if (tie)
-                        c = rank_in_bucket_full(seed, cell, s, s_word + lo, hi - lo, wv & 255u);
-                    s_perm[lo + c] = (uint16_t)(wv & 255u);
+                        c = rank_in_bucket_full(seed, cell, s, s_word + lo, hi - lo, wv & RM, RM);
+                    s_perm[lo + c] = (uint16_t)(wv & RM);
                 }
             }
             __syncwarp();

@@ -81,6 +81,7 @@ struct Plan {
     std::vector<Buf> bufs;
     int64_t bytes = 0;
     sdm_tuning tuning{}; // the launch tuning the plan was built with
+    std::vector<unsigned char> host_pack; // the tables uploaded in one copy
 };
 
 struct SedBuffers; // second layout and scratch of the sedimentation step (sdm_sediment.cu)
@@ -211,7 +212,7 @@ size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
 // tuning (sdm_set_tuning) picks one variant per size class when a plan is
 // built.
 #define SDM_WARP_VARIANTS(X)                                                                                           \
-    X(64, 1) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(128, 4) X(256, 1) X(256, 2) X(256, 4)
+    X(64, 1) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(128, 4) X(256, 1) X(256, 2) X(256, 4) X(512, 1) X(512, 2) X(512, 4)
 #define SDM_BLOCK_VARIANTS(X)                                                                                          \
     X(64, 32, 4) X(128, 64, 4) X(256, 128, 4) X(512, 256, 4) X(1024, 512, 3) X(2048, 1024, 2) X(4096, 1024, 2)
 
@@ -250,7 +251,7 @@ constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 int g_spec_grid = 1; // blocks of the total-spectrum kernel (resident blocks x SMs)
 
 std::mutex g_tuning_mutex;
-sdm_tuning g_tuning = {4096, 256, 2, 0};
+sdm_tuning g_tuning = {4096, 512, 2, 0};
 
 bool same_tuning(const sdm_tuning &a, const sdm_tuning &b)
 {
@@ -336,13 +337,14 @@ void launch_variant(int v, int n, const WorkItem *items, InstDev *const *insts, 
     x.launch(grid, n, items, insts, off, st);
 }
 
-// Size class of a cell of n stored SDs under the tuning; -1: multi-pass path.
+// Size class of a cell of n >= 2 stored SDs under the tuning (the smallest
+// class capacity 64 2^c >= n); -1: the multi-pass path.
 int class_of(int n, const sdm_tuning &t)
 {
-    for (int c = 0; c < kNumClass; ++c)
-        if (n <= kClassCap[c])
-            return kClassCap[c] <= t.smem_max_sd ? c : -1;
-    return -1;
+    const int c = n <= 64 ? 0 : 32 - __builtin_clz((unsigned)(n - 1)) - 6;
+    if (c >= kNumClass || kClassCap[c] > t.smem_max_sd)
+        return -1;
+    return c;
 }
 
 // Work lists of every run in the batch, split by cell size.
@@ -360,6 +362,13 @@ sdm_status build_plan(sdm_batch *b)
     int64_t hist_total = 0, sd_total = 0, bkt_total = 0;
     const sdm_tuning tun = current_tuning();
     pl.tuning = tun;
+    {
+        int64_t cells = 0;
+        for (int i = 0; i < n_inst; ++i)
+            cells += b->ctxs[i]->cfg.n_cells;
+        for (int k = 0; k < kNumClass; ++k)
+            items[k].reserve((size_t)cells);
+    }
     for (int k = 0; k < kNumClass; ++k)
         pl.variant[k] = variant_for(kClassCap[k], tun);
     for (int i = 0; i < n_inst; ++i) {
@@ -398,30 +407,52 @@ sdm_status build_plan(sdm_batch *b)
             bigs.push_back(bc);
         }
     }
+    // every table (the runs, the work list of each class, the big-cell
+    // descriptors) in one host buffer, one device buffer and one copy
     pl.n_inst = n_inst;
-    pl.d_insts = plan_alloc<InstDev *>(pl, mem, n_inst);
-    if (!pl.d_insts)
-        return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
-    cudaError_t e = cudaMemcpyAsync(pl.d_insts, insts.data(), sizeof(InstDev *) * n_inst, cudaMemcpyHostToDevice, b->stream);
-    for (int k = 0; k < kNumClass && e == cudaSuccess; ++k) {
-        pl.n_items[k] = (int)items[k].size();
-        if (!pl.n_items[k])
-            continue;
-        pl.d_items[k] = plan_alloc<WorkItem>(pl, mem, items[k].size());
-        if (!pl.d_items[k])
-            return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
-        e = cudaMemcpyAsync(pl.d_items[k], items[k].data(), sizeof(WorkItem) * items[k].size(), cudaMemcpyHostToDevice,
-                            b->stream);
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t off_items[kNumClass], sz = a16(sizeof(InstDev *) * n_inst);
+    for (int k = 0; k < kNumClass; ++k) {
+        off_items[k] = sz;
+        sz += a16(sizeof(WorkItem) * items[k].size());
     }
-    if (e == cudaSuccess && !bigs.empty()) {
+    const size_t off_bigs = sz;
+    sz += a16(sizeof(BigCell) * bigs.size());
+    const size_t off_chunks = sz;
+    sz += a16(sizeof(BigChunk) * chunks.size());
+    const size_t off_buckets = sz;
+    sz += a16(sizeof(BigBucket) * buckets.size());
+    const size_t off_pairs = sz;
+    sz += a16(sizeof(BigPairs) * pairs.size());
+    pl.host_pack.assign(sz, 0);
+    unsigned char *h = pl.host_pack.data();
+    std::memcpy(h, insts.data(), sizeof(InstDev *) * n_inst);
+    for (int k = 0; k < kNumClass; ++k)
+        if (!items[k].empty())
+            std::memcpy(h + off_items[k], items[k].data(), sizeof(WorkItem) * items[k].size());
+    if (!bigs.empty()) {
+        std::memcpy(h + off_bigs, bigs.data(), sizeof(BigCell) * bigs.size());
+        std::memcpy(h + off_chunks, chunks.data(), sizeof(BigChunk) * chunks.size());
+        std::memcpy(h + off_buckets, buckets.data(), sizeof(BigBucket) * buckets.size());
+        std::memcpy(h + off_pairs, pairs.data(), sizeof(BigPairs) * pairs.size());
+    }
+    unsigned char *d = plan_alloc<unsigned char>(pl, mem, sz);
+    if (!d)
+        return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
+    pl.d_insts = reinterpret_cast<InstDev **>(d);
+    for (int k = 0; k < kNumClass; ++k) {
+        pl.n_items[k] = (int)items[k].size();
+        pl.d_items[k] = pl.n_items[k] ? reinterpret_cast<WorkItem *>(d + off_items[k]) : nullptr;
+    }
+    if (!bigs.empty()) {
         pl.n_big = (int)bigs.size();
         pl.n_chunks = (int)chunks.size();
         pl.n_buckets = (int)buckets.size();
         pl.n_pair_blocks = (int)pairs.size();
-        pl.d_bigs = plan_alloc<BigCell>(pl, mem, bigs.size());
-        pl.d_chunks = plan_alloc<BigChunk>(pl, mem, chunks.size());
-        pl.d_buckets = plan_alloc<BigBucket>(pl, mem, buckets.size());
-        pl.d_pairs = plan_alloc<BigPairs>(pl, mem, pairs.size());
+        pl.d_bigs = reinterpret_cast<BigCell *>(d + off_bigs);
+        pl.d_chunks = reinterpret_cast<BigChunk *>(d + off_chunks);
+        pl.d_buckets = reinterpret_cast<BigBucket *>(d + off_buckets);
+        pl.d_pairs = reinterpret_cast<BigPairs *>(d + off_pairs);
         pl.scratch.hist = plan_alloc<uint32_t>(pl, mem, hist_total);
         pl.scratch.bstart = plan_alloc<uint32_t>(pl, mem, bkt_total);
         pl.scratch.key = plan_alloc<uint64_t>(pl, mem, sd_total);
@@ -429,22 +460,12 @@ sdm_status build_plan(sdm_batch *b)
         pl.scratch.perm = plan_alloc<uint32_t>(pl, mem, sd_total);
         pl.scratch.scale = plan_alloc<double>(pl, mem, bigs.size());
         pl.scratch.scale_f = plan_alloc<float>(pl, mem, bigs.size());
-        if (!pl.d_bigs || !pl.d_chunks || !pl.d_buckets || !pl.d_pairs || !pl.scratch.hist || !pl.scratch.bstart ||
-            !pl.scratch.key || !pl.scratch.rank || !pl.scratch.perm || !pl.scratch.scale || !pl.scratch.scale_f)
+        if (!pl.scratch.hist || !pl.scratch.bstart || !pl.scratch.key || !pl.scratch.rank || !pl.scratch.perm ||
+            !pl.scratch.scale || !pl.scratch.scale_f)
             return fail(&b->error, SDM_ENOMEM, "batch plan: big-cell scratch allocation failed");
-        e = cudaMemcpyAsync(pl.d_bigs, bigs.data(), sizeof(BigCell) * bigs.size(), cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pl.d_chunks, chunks.data(), sizeof(BigChunk) * chunks.size(), cudaMemcpyHostToDevice,
-                                b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pl.d_buckets, buckets.data(), sizeof(BigBucket) * buckets.size(),
-                                cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(pl.d_pairs, pairs.data(), sizeof(BigPairs) * pairs.size(), cudaMemcpyHostToDevice,
-                                b->stream);
     }
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(b->stream); // host vectors above go out of scope
+    // the host copy lives as long as the plan: no wait for the upload
+    const cudaError_t e = cudaMemcpyAsync(d, h, sz, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess)
         return cuda_fail(b, e, "batch plan upload");
     return SDM_OK;
@@ -1097,16 +1118,16 @@ sdm_status sdm_batch_destroy(sdm_batch *batch)
 
 sdm_status sdm_set_tuning(const sdm_tuning *t)
 {
-    sdm_tuning v = {4096, 256, 2, 0};
+    sdm_tuning v = {4096, 512, 2, 0};
     if (t) {
         const bool smem_ok = t->smem_max_sd == 512 || t->smem_max_sd == 1024 || t->smem_max_sd == 2048 ||
                              t->smem_max_sd == 4096;
         const bool warp_ok = t->warp_cell_max == 0 || t->warp_cell_max == 64 || t->warp_cell_max == 128 ||
-                             t->warp_cell_max == 256;
+                             t->warp_cell_max == 256 || t->warp_cell_max == 512;
         const bool wpb_ok = t->warps_per_block == 1 || t->warps_per_block == 2 || t->warps_per_block == 4;
         if (!smem_ok || !warp_ok || !wpb_ok || t->reserved0 != 0 || t->warp_cell_max > t->smem_max_sd)
             return fail(nullptr, SDM_EINVAL,
-                        "tuning: smem_max_sd in {512,1024,2048,4096}, warp_cell_max in {0,64,128,256} and <= "
+                        "tuning: smem_max_sd in {512,1024,2048,4096}, warp_cell_max in {0,64,128,256,512} and <= "
                         "smem_max_sd, warps_per_block in {1,2,4}, reserved0 = 0");
         v = *t;
     }

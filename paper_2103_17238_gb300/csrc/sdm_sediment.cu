@@ -226,34 +226,33 @@ __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restri
     __shared__ uint32_t s_warp[32];
     __shared__ double s_pr[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int per = (n_groups + 1023) / 1024;
-    const int a = min(n_groups, t * per), b = min(n_groups, a + per);
-    uint32_t su = 0, sp = 0;
-    for (int g = a; g < b; ++g) {
-        su += counts[g];
-        sp += (counts[g] + 1u) & ~1u;
-    }
-    s_u[t] = su;
-    s_p[t] = sp;
-    __syncthreads();
-    const uint32_t tu = block_exclusive_scan<1024, 1024>(s_u, s_warp);
-    const uint32_t tp = block_exclusive_scan<1024, 1024>(s_p, s_warp);
-    uint32_t ru = s_u[t], rp = s_p[t];
-    for (int g = a; g < b; ++g) {
-        ustart[g] = (int32_t)ru;
-        poff[g] = (int32_t)rp;
-        ru += counts[g];
-        rp += (counts[g] + 1u) & ~1u;
+    // tiles of 1024 groups (coalesced), running totals carried over
+    uint32_t cu = 0, cp = 0;
+    for (int32_t g0 = 0; g0 < n_groups; g0 += 1024) {
+        const int32_t g = g0 + t;
+        const uint32_t c = g < n_groups ? counts[g] : 0u;
+        s_u[t] = c;
+        s_p[t] = (c + 1u) & ~1u;
+        __syncthreads();
+        const uint32_t tu = block_exclusive_scan<1024, 1024>(s_u, s_warp);
+        const uint32_t tp = block_exclusive_scan<1024, 1024>(s_p, s_warp);
+        if (g < n_groups) {
+            ustart[g] = (int32_t)(cu + s_u[t]);
+            poff[g] = (int32_t)(cp + s_p[t]);
+        }
+        cu += tu;
+        cp += tp;
+        __syncthreads();
     }
     if (t == 0) {
-        ustart[n_groups] = (int32_t)tu;
-        poff[n_groups] = (int32_t)tp;
+        ustart[n_groups] = (int32_t)cu;
+        poff[n_groups] = (int32_t)cp;
     }
-    const int pper = (n_parts + 1023) / 1024;
-    const int pa = min(n_parts, t * pper), pb = min(n_parts, pa + pper);
+    // the precipitated water: thread t sums parts t, t + 1024, ... in order,
+    // then a fixed tree over the threads
     double pr = 0.0;
-    for (int c = pa; c < pb; ++c)
-        pr = __dadd_rn(pr, precip[c]);
+    for (int i = t; i < n_parts; i += 1024)
+        pr = __dadd_rn(pr, precip[i]);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1)
         pr = __dadd_rn(pr, __shfl_down_sync(0xFFFFFFFFu, pr, d));

@@ -96,7 +96,7 @@ def test_tuning_round_trip_and_validation(lib):
     range (the previous setting stays), restored by NULL."""
     from paper_2103_17238_gb300 import sdm
 
-    default = {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2}
+    default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2}
     sdm.sdm_set_tuning(None)
     assert sdm.sdm_get_tuning() == default
     t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4}
@@ -104,7 +104,8 @@ def test_tuning_round_trip_and_validation(lib):
     assert sdm.sdm_get_tuning() == t
     for bad in ({"smem_max_sd": 8192, "warp_cell_max": 256, "warps_per_block": 2},
                 {"smem_max_sd": 1000, "warp_cell_max": 256, "warps_per_block": 2},
-                {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2},
+                {"smem_max_sd": 4096, "warp_cell_max": 1024, "warps_per_block": 2},
+                {"smem_max_sd": 512, "warp_cell_max": 1024, "warps_per_block": 2},
                 {"smem_max_sd": 4096, "warp_cell_max": 96, "warps_per_block": 2},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 3},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 0}):
@@ -130,7 +131,7 @@ def test_autotune_candidates_are_valid_and_signature_is_stable(lib):
         seen.add(tuple(sorted(c.items())))
     sdm.sdm_set_tuning(None)
     assert len(seen) == len(autotune.CANDIDATES)
-    assert {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2} in autotune.CANDIDATES
+    assert {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2} in autotune.CANDIDATES
 
     class FakeRun:
         def __init__(self, kernel, n_cells, largest):

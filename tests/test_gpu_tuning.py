@@ -17,7 +17,7 @@ SIZES = [0, 1, 2, 3, 31, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 102
          4096, 4097, 6000]
 
 TUNINGS = [dict(smem_max_sd=s, warp_cell_max=w, warps_per_block=k)
-           for s, w, k in itertools.product((512, 1024, 2048, 4096), (0, 64, 128, 256), (1, 2, 4))
+           for s, w, k in itertools.product((512, 1024, 2048, 4096), (0, 64, 128, 256, 512), (1, 2, 4))
            if not (w == 0 and k != 2)]
 
 
