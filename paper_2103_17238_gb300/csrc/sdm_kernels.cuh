@@ -987,8 +987,41 @@ __global__ void __launch_bounds__(kBigNT) big_hist_kernel(const BigChunk *__rest
         h[i] = s_hist[i];
 }
 
-// One CTA per big cell: per bucket, the running prefix over chunks (in place)
-// and the bucket total; then bucket starts; the cell's scale factor.
+// Per bucket of a big cell, the running prefix of its counts over the chunks
+// (in place) and the bucket total (into the bucket-start array, scanned
+// next).  Block (big, tile) takes buckets 256 tile .. 256 tile + 255 of big
+// cell `big`; each thread loads its column kBigColU chunks at a time.
+constexpr int kBigColNT = 256;
+constexpr int kBigColU = 16;
+
+__global__ void __launch_bounds__(kBigColNT) big_colscan_kernel(const BigCell *__restrict__ bigs, int32_t max_tiles,
+                                                                BigScratch S)
+{
+    const int big = blockIdx.x / max_tiles, tile = blockIdx.x - big * max_tiles;
+    const BigCell bc = bigs[big];
+    const int NB = 1 << bc.lb;
+    const int b = tile * kBigColNT + threadIdx.x;
+    if (b >= NB)
+        return;
+    uint32_t *h = S.hist + bc.hist_base;
+    uint32_t run = 0;
+    for (int c0 = 0; c0 < bc.n_chunks; c0 += kBigColU) {
+        uint32_t x[kBigColU];
+#pragma unroll
+        for (int u = 0; u < kBigColU; ++u)
+            x[u] = c0 + u < bc.n_chunks ? h[(int64_t)(c0 + u) * NB + b] : 0u;
+#pragma unroll
+        for (int u = 0; u < kBigColU; ++u) {
+            if (c0 + u < bc.n_chunks)
+                h[(int64_t)(c0 + u) * NB + b] = run;
+            run += x[u];
+        }
+    }
+    S.bstart[bc.bkt_base + b] = run;
+}
+
+// One CTA per big cell: bucket starts from the bucket totals; the cell's
+// scale factor.
 __global__ void __launch_bounds__(kBigNT) big_scan_kernel(const BigCell *__restrict__ bigs,
                                                           const InstDev *const *__restrict__ insts, BigScratch S)
 {
@@ -997,16 +1030,8 @@ __global__ void __launch_bounds__(kBigNT) big_scan_kernel(const BigCell *__restr
     __shared__ uint32_t s_warp[32];
     const BigCell bc = bigs[blockIdx.x];
     const int NB = 1 << bc.lb;
-    uint32_t *h = S.hist + bc.hist_base;
-    for (int b = threadIdx.x; b < NB; b += kBigNT) {
-        uint32_t run = 0;
-        for (int c = 0; c < bc.n_chunks; ++c) {
-            const uint32_t x = h[(int64_t)c * NB + b];
-            h[(int64_t)c * NB + b] = run;
-            run += x;
-        }
-        s_tot[b] = run;
-    }
+    for (int b = threadIdx.x; b < NB; b += kBigNT)
+        s_tot[b] = S.bstart[bc.bkt_base + b];
     for (int b = NB + threadIdx.x; b < (1 << kBigMaxLB); b += kBigNT)
         s_tot[b] = 0u;
     __syncthreads();

@@ -177,6 +177,8 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     InstDev *const *insts = reinterpret_cast<InstDev *const *>(base + kNaInsts);
     const size_t hs = big_hist_smem(lb);
     big_hist_kernel<<<n_chunks, kBigNT, hs, s>>>(chunks, big, insts, S, 0);
+    const int tiles = std::max(1, (1 << lb) / kBigColNT);
+    big_colscan_kernel<<<tiles, kBigColNT, 0, s>>>(big, tiles, S);
     big_scan_kernel<<<1, kBigNT, big_hist_smem(kBigMaxLB), s>>>(big, insts, S);
     big_scatter_kernel<<<n_chunks, kBigNT, hs, s>>>(chunks, big, insts, S, 0);
     big_bucket_sort_kernel<<<1 << lb, kBucketNT, 0, s>>>(buckets, big, S);

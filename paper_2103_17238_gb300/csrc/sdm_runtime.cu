@@ -480,6 +480,8 @@ void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
     if (pl.n_big) {
         const size_t hs = big_hist_smem(pl.max_big_lb);
         big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
+        const int tiles = std::max(1, (1 << pl.max_big_lb) / kBigColNT);
+        big_colscan_kernel<<<pl.n_big * tiles, kBigColNT, 0, st>>>(pl.d_bigs, tiles, pl.scratch);
         big_scan_kernel<<<pl.n_big, kBigNT, big_hist_smem(kBigMaxLB), st>>>(pl.d_bigs, pl.d_insts, pl.scratch);
         big_scatter_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
         big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.scratch);
