@@ -261,6 +261,36 @@ def test_sort_keys_sharing_their_top_bits(env):
     run.close()
 
 
+@pytest.mark.parametrize("kernel,precision", [("geometric", "fp64"), ("golovin", "fp64"), ("geometric", "kfp32")])
+def test_extreme_multiplicities(env, kernel, precision):
+    """Multiplicities across the int64 range (1, 2^31 - 1, 2^32 + 1, 2^53 + 1,
+    2^62, ...): the conversions past 32 and 53 bits, the cap with g xi_k past
+    2^64, and large products in the update, with p from small to huge."""
+    O, sdm, torch = env
+    rng = np.random.default_rng(41)
+    sizes = [2, 3, 64, 65, 255, 256, 511, 700, 5000]
+    cell = np.concatenate([np.full(n, c, np.int32) for c, n in enumerate(sizes)])
+    n = len(cell)
+    choices = np.array([1, 2, 3, 1000, 2**31 - 1, 2**32 + 1, 2**40 + 7, 2**53 + 1, 2**60, 2**62, 2**62 + 12345],
+                       dtype=np.int64)
+    xi = choices[rng.integers(0, len(choices), n)]
+    wide = rng.random(n) < 0.3
+    xi[wide] = rng.integers(1, 2**62, int(wide.sum()))
+    r = np.exp(rng.uniform(np.log(1e-6), np.log(3e-3), n))
+    v = 4 / 3 * np.pi * r**3
+    perm = rng.permutation(n)
+    xi, v, cell = xi[perm], v[perm], cell[perm]
+    for dv in (1e30, 1e6, 1e-6):
+        run = _gpu_run(sdm, kernel, precision, xi, v, cell, len(sizes), dv, 5, 3)
+        gx, gv = run.attributes()
+        st = _oracle_run(O, kernel, precision, xi, v, cell, len(sizes), dv, 5, 3)
+        _assert_same(gx, gv, st, f"extreme xi, dv={dv}")
+        got = run.spectrum(I.R_EDGES)
+        want = O.spectrum(O.params(kernel, precision, dv=dv), st, I.R_EDGES)
+        assert np.allclose(got, want, rtol=1e-12, atol=0)
+        run.close()
+
+
 def test_device_inputs_and_outputs(env):
     O, sdm, torch = env
     g = I.grid_geometric(side=4, sd_per_cell=200, seed=8)
