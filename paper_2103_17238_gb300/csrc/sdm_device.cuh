@@ -32,6 +32,8 @@ struct InstDev {
     double k1, k2, k3, r1, r2;
     float bf, k1f, k2f, k3f, r1f, r2f; // binary32 roundings of the above
     float dtdvf;                       // dt / dv rounded to binary32 (filter only)
+    float pre_c[3];  // pre-filter: p <= pre_c[regime] f(v_max) xi_j scale (rounded up; pair_prefilter_zero)
+    float pre_v[2];  // pre-filter: volumes of the regime bounds r1, r2 (rounded down)
     int32_t kernel, precision, n_cells;
     uint32_t status; // bit 0: a bounded device wait gave up (reported as SDM_ETIMEOUT)
 };
@@ -268,6 +270,7 @@ __device__ __forceinline__ double cell_scale(double dtdv, int64_t n_c)
 struct PairConsts {
     float bf, k1f, k2f, k3f, r1f, r2f;
     float dtdvf;                  // dt / dV rounded to binary32 (filter only)
+    float pre_c[3], pre_v[2];     // the pre-filter's constants
     float r1_lo, r1_hi, r2_lo, r2_hi; // regime bounds widened by 2^-14 (filter only)
     int32_t kernel, precision;
 };
@@ -282,6 +285,11 @@ __device__ __forceinline__ PairConsts pair_consts(const InstDev *P)
     c.r1f = P->r1f;
     c.r2f = P->r2f;
     c.dtdvf = P->dtdvf;
+    c.pre_c[0] = P->pre_c[0];
+    c.pre_c[1] = P->pre_c[1];
+    c.pre_c[2] = P->pre_c[2];
+    c.pre_v[0] = P->pre_v[0];
+    c.pre_v[1] = P->pre_v[1];
     c.r1_lo = c.r1f * (1.0f - 0x1p-14f);
     c.r1_hi = c.r1f * (1.0f + 0x1p-14f);
     c.r2_lo = c.r2f * (1.0f - 0x1p-14f);
@@ -426,6 +434,48 @@ __device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float 
     if (!ok || ceilf(lo) != m || !(m <= 65536.0f))
         return -1;
     return (int32_t)m;
+}
+
+// A bound that settles most pairs before the filter: gamma = 0 is certain
+// when p < u, and p <= B xi_j scale.  Golovin: K = b (v_j + v_k) <= 2 b v_max.
+// Geometric: the fall speed never decreases with r (the Rogers-Yau regimes
+// join with upward steps), so K = pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)| <=
+// 4 pi r_max^2 v_t(r_max), which in each regime is
+//   r < r1:       4 pi k1 r^4    = C1 v^(4/3),  C1 = 4 pi k1 (3 / (4 pi))^(4/3)
+//   r1 <= r < r2: 4 pi k2 r^3    = 3 k2 v
+//   r >= r2:      4 pi k3 r^(5/2) = C3 v^(5/6), C3 = 4 pi k3 (3 / (4 pi))^(5/6).
+// The regime is chosen from v_max (1 + 2^-10): near a bound the upper
+// regime's formula, which is the larger one there (its speed jumps up),
+// covers both sides.  pre_c (2 b, C1, 3 k2, C3) is rounded up and the regime
+// volumes down on the host.  The binary32 evaluation underestimates B xi_j
+// scale by less than 2^-15 (truncated v and xi, the scale's rounding, three
+// products, lg2/ex2 approximations for the powers), and the exact p (binary64,
+// or binary32 with the 1-ulp radius) exceeds the bound's real value by less
+// than 2^-17: so bound (1 + 2^-8) < u_lo (u's exact lower bound) proves
+// p < u.  Out-of-range or underflowing values abstain (return false).
+__device__ __forceinline__ bool pair_prefilter_zero(const PairConsts &C, float sc, int64_t xi_j, uint32_t vj_hi,
+                                                    uint32_t vk_hi, uint32_t wa)
+{
+    bool ok, ok_k;
+    const float vjf = hi2f(vj_hi, ok), vkf = hi2f(vk_hi, ok_k);
+    ok &= ok_k;
+    const float vmax = fmaxf(vjf, vkf);
+    float bound;
+    if (C.kernel == KERNEL_GOLOVIN) {
+        bound = C.pre_c[0] * vmax;
+    } else {
+        const float vup = vmax * (1.0f + 0x1p-10f);
+        if (vup < C.pre_v[1] && !(vup < C.pre_v[0])) {
+            bound = C.pre_c[1] * vmax;
+        } else {
+            const bool stokes = vup < C.pre_v[0];
+            const float t = ex2_approx(lg2_approx(vmax) * (stokes ? 4.0f / 3.0f : 5.0f / 6.0f));
+            ok &= t >= 0x1p-100f;
+            bound = (stokes ? C.pre_c[0] : C.pre_c[2]) * t;
+        }
+    }
+    bound = (bound * xi2f(xi_j)) * sc;
+    return ok && bound * (1.0f + 0x1p-8f) < uniform_lo23(wa);
 }
 
 // The same from full binary64 volumes.

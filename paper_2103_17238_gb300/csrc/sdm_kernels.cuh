@@ -808,26 +808,30 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             }
             __syncwarp();
 
-            // pairs (l = 2q, 2q + 1 share one Philox block): the filter
-            // settles most; colliding and undecided ones join the queue
+            // pairs (l = 2q, 2q + 1 share one Philox block).  A bound settles
+            // most of them (gamma = 0); the rest are compacted into the sort
+            // arrays, dead by now (2 CAP words hold 2 CAP / 3 >= CAP / 2
+            // entries of 3 words: every pair fits), and go through the full
+            // filter one per lane: certain collisions are updated at once,
+            // undecided pairs join the queue for the exact evaluation.
             const uint32_t n_pairs = n_c / 2;
             const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
             const PairConsts C = pair_consts(P);
+            const float sc = C.dtdvf * ratio_f;
             const uint32_t n_q = (n_pairs + 1) / 2;
             const uint32_t *vs_words = reinterpret_cast<const uint32_t *>(vs);
+            uint32_t *todo = s_word;
+            uint32_t n_todo = 0; // warp-uniform
             for (uint32_t q0 = 0; q0 < n_q; q0 += 32) { // warp-uniform trip count
                 const uint32_t q = q0 + lane;
                 const uint4 w = draw4(seed, q, cell, s, 1u);
-                uint32_t A[2], B[2];
-                int32_t gf[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t l = 2 * q + h;
-                    A[h] = 0;
-                    B[h] = 0;
-                    gf[h] = 0;
+                    bool need = false;
+                    uint32_t ab = 0;
                     if (q < n_q && l < n_pairs) {
-                        const uint32_t ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
+                        ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
                         uint32_t a = ab & 0xFFFFu, b = ab >> 16;
                         int64_t xa = xs[a];
                         const int64_t xb = xs[b];
@@ -837,62 +841,78 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                             b = tmp;
                             xa = xb;
                         }
-                        A[h] = a;
-                        B[h] = b;
-                        gf[h] = pair_gamma_filter(C, ratio_f, xa, vs_words[2 * a + 1], vs_words[2 * b + 1],
-                                                  h ? w.z : w.x);
+                        ab = a | (b << 16);
+                        need = !pair_prefilter_zero(C, sc, xa, vs_words[2 * a + 1], vs_words[2 * b + 1],
+                                                    h ? w.z : w.x);
                     }
+                    const unsigned m = __ballot_sync(FULL, need);
+                    if (need) {
+                        const uint32_t idx = n_todo + __popc(m & ((1u << lane) - 1u));
+                        todo[3 * idx] = ab;
+                        todo[3 * idx + 1] = h ? w.z : w.x;
+                        todo[3 * idx + 2] = h ? w.w : w.y;
+                    }
+                    n_todo += __popc(m);
                 }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t a = A[h], b = B[h];
-                    if (gf[h] > 0) { // a certain collision: update from the staged state now
-                        int64_t xa = xs[a], xb = xs[b];
-                        double va = vs[a], vb = vs[b];
-                        const bool split = shima_update(cap_gamma(gf[h], xa, xb), xa, xb, va, vb);
-                        gxi[a] = xa;
-                        gxi[b] = xb;
-                        gv[b] = vb;
-                        if (split)
-                            gv[a] = va;
-                    }
-                    // pairs the filter could not decide wait for the exact evaluation
-                    const bool und = gf[h] < 0;
-                    const unsigned m = __ballot_sync(FULL, und);
-                    if (m) {
-                        const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
-                        const uint32_t base = s_qn;
-                        const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
-                        if (und) {
-                            if (idx < (uint32_t)kWarpQueue) {
-                                WQEntry E;
-                                E.slot_j = (uint32_t)(meta.x + (int)a);
-                                E.slot_k = (uint32_t)(meta.x + (int)b);
-                                E.wa = wa;
-                                E.wb = wb;
-                                E.n_c = n_c;
-                                E.inst = meta.w;
-                                E.gamma = -1;
-                                s_q[idx] = E;
-                            } else { // queue full: evaluate here
-                                int64_t xa = xs[a], xb = xs[b];
-                                double va = vs[a], vb = vs[b];
-                                const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
-                                if (g > 0) {
-                                    const bool split = shima_update(g, xa, xb, va, vb);
-                                    gxi[a] = xa;
-                                    gxi[b] = xb;
-                                    gv[b] = vb;
-                                    if (split)
-                                        gv[a] = va;
-                                }
+            }
+            __syncwarp();
+            for (uint32_t e0 = 0; e0 < n_todo; e0 += 32) { // warp-uniform trip count
+                const uint32_t e = e0 + lane;
+                uint32_t a = 0, b = 0, wa = 0, wb = 0;
+                int32_t gf = 0;
+                if (e < n_todo) {
+                    const uint32_t ab = todo[3 * e];
+                    a = ab & 0xFFFFu;
+                    b = ab >> 16;
+                    wa = todo[3 * e + 1];
+                    wb = todo[3 * e + 2];
+                    gf = pair_gamma_filter(C, ratio_f, xs[a], vs_words[2 * a + 1], vs_words[2 * b + 1], wa);
+                }
+                if (gf > 0) { // a certain collision: update from the staged state now
+                    int64_t xa = xs[a], xb = xs[b];
+                    double va = vs[a], vb = vs[b];
+                    const bool split = shima_update(cap_gamma(gf, xa, xb), xa, xb, va, vb);
+                    gxi[a] = xa;
+                    gxi[b] = xb;
+                    gv[b] = vb;
+                    if (split)
+                        gv[a] = va;
+                }
+                // pairs the filter could not decide wait for the exact evaluation
+                const bool und = gf < 0;
+                const unsigned m = __ballot_sync(FULL, und);
+                if (m) {
+                    const uint32_t base = s_qn;
+                    const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
+                    if (und) {
+                        if (idx < (uint32_t)kWarpQueue) {
+                            WQEntry E;
+                            E.slot_j = (uint32_t)(meta.x + (int)a);
+                            E.slot_k = (uint32_t)(meta.x + (int)b);
+                            E.wa = wa;
+                            E.wb = wb;
+                            E.n_c = n_c;
+                            E.inst = meta.w;
+                            E.gamma = -1;
+                            s_q[idx] = E;
+                        } else { // queue full: evaluate here
+                            int64_t xa = xs[a], xb = xs[b];
+                            double va = vs[a], vb = vs[b];
+                            const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                            if (g > 0) {
+                                const bool split = shima_update(g, xa, xb, va, vb);
+                                gxi[a] = xa;
+                                gxi[b] = xb;
+                                gv[b] = vb;
+                                if (split)
+                                    gv[a] = va;
                             }
                         }
-                        __syncwarp();
-                        if (lane == 0)
-                            s_qn = base + (uint32_t)__popc(m);
-                        __syncwarp();
                     }
+                    __syncwarp();
+                    if (lane == 0)
+                        s_qn = base + (uint32_t)__popc(m);
+                    __syncwarp();
                 }
             }
         }

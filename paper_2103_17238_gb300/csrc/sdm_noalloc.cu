@@ -155,6 +155,7 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     inst.r2f = (float)inst.r2;
     inst.dtdvf = (float)inst.dtdv;
     inst.kernel = cfg->kernel;
+    set_prefilter(inst);
     inst.precision = cfg->precision;
     inst.n_cells = 1;
     const int n = (int)n_sd;

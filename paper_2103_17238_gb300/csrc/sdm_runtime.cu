@@ -656,6 +656,27 @@ sdm_status check_config(const sdm_config *cfg, std::string *err)
     return SDM_OK;
 }
 
+// The pre-filter's constants (pair_prefilter_zero), rounded up to binary32
+// with a 2^-20 pad: Golovin 2 b; geometric C1 = 4 pi k1 (3 / (4 pi))^(4/3),
+// 3 k2, C3 = 4 pi k3 (3 / (4 pi))^(5/6).  The regime volumes 4/3 pi r^3,
+// rounded down.
+void set_prefilter(InstDev &d)
+{
+    const double pi = 3.141592653589793;
+    auto up = [](double x) { return std::nextafter((float)(x * (1.0 + 0x1p-20)), INFINITY); };
+    auto down = [](double x) { return std::nextafter((float)(x * (1.0 - 0x1p-20)), 0.0f); };
+    if (d.kernel == SDM_KERNEL_GOLOVIN) {
+        d.pre_c[0] = up(2.0 * d.b);
+        d.pre_c[1] = d.pre_c[2] = d.pre_c[0];
+    } else {
+        d.pre_c[0] = up(4.0 * pi * d.k1 * std::pow(0.75 / pi, 4.0 / 3.0));
+        d.pre_c[1] = up(3.0 * d.k2);
+        d.pre_c[2] = up(4.0 * pi * d.k3 * std::pow(0.75 / pi, 5.0 / 6.0));
+    }
+    d.pre_v[0] = down(4.0 / 3.0 * pi * d.r1 * d.r1 * d.r1);
+    d.pre_v[1] = down(4.0 / 3.0 * pi * d.r2 * d.r2 * d.r2);
+}
+
 InstDev make_inst(const sdm_ctx *c)
 {
     InstDev d{};
@@ -681,6 +702,7 @@ InstDev make_inst(const sdm_ctx *c)
     d.kernel = c->cfg.kernel;
     d.precision = c->cfg.precision;
     d.n_cells = c->cfg.n_cells;
+    set_prefilter(d);
     return d;
 }
 
