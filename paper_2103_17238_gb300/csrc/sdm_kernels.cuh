@@ -682,9 +682,10 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                 word[i] = (kw[r].x & ~RM) | (uint32_t)(2 * q);
                 word[i + 1] = (kw[r].z & ~RM) | (uint32_t)(2 * q + 1);
                 if (2 * q < n) {
-                    if (xs[2 * q] > 0)
+                    const longlong2 x2 = reinterpret_cast<const longlong2 *>(xs)[q];
+                    if (x2.x > 0)
                         slot[i] = atomicAdd(&s_hist[word[i] >> (32 - LB)], 1u);
-                    if (xs[2 * q + 1] > 0)
+                    if (x2.y > 0)
                         slot[i + 1] = atomicAdd(&s_hist[word[i + 1] >> (32 - LB)], 1u);
                 }
             }
@@ -822,35 +823,45 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
             const uint32_t *vs_words = reinterpret_cast<const uint32_t *>(vs);
             uint32_t *todo = s_word;
             uint32_t n_todo = 0; // warp-uniform
-            for (uint32_t q0 = 0; q0 < n_q; q0 += 32) { // warp-uniform trip count
-                const uint32_t q = q0 + lane;
-                const uint4 w = draw4(seed, q, cell, s, 1u);
+            // QG Philox blocks per lane are drawn, and their pairs bounded,
+            // before any compaction, so that the independent chains interleave.
+            constexpr int QG = CAP >= 256 ? 2 : 1;
+            for (uint32_t q0 = 0; q0 < n_q; q0 += 32 * QG) { // warp-uniform trip count
+                uint4 w[QG];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t l = 2 * q + h;
-                    bool need = false;
-                    uint32_t ab = 0;
-                    if (q < n_q && l < n_pairs) {
-                        ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
-                        uint32_t a = ab & 0xFFFFu, b = ab >> 16;
-                        int64_t xa = xs[a];
-                        const int64_t xb = xs[b];
-                        if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
-                            const uint32_t tmp = a;
-                            a = b;
-                            b = tmp;
-                            xa = xb;
+                for (int r = 0; r < QG; ++r)
+                    w[r] = draw4(seed, q0 + lane + 32 * r, cell, s, 1u);
+                bool need[2 * QG];
+                uint32_t abv[2 * QG];
+#pragma unroll
+                for (int r = 0; r < QG; ++r) {
+                    const uint32_t q = q0 + lane + 32 * r;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t l = 2 * q + h;
+                        need[2 * r + h] = false;
+                        abv[2 * r + h] = 0;
+                        if (q < n_q && l < n_pairs) {
+                            // the bound needs xi_j = max(xi_a, xi_b) only; which of the
+                            // two is j is settled in the full pass
+                            const uint32_t ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
+                            const uint32_t a = ab & 0xFFFFu, b = ab >> 16;
+                            const int64_t xa = xs[a], xb = xs[b];
+                            abv[2 * r + h] = ab;
+                            need[2 * r + h] = !pair_prefilter_zero(C, sc, xa > xb ? xa : xb, vs_words[2 * a + 1],
+                                                                   vs_words[2 * b + 1], h ? w[r].z : w[r].x);
                         }
-                        ab = a | (b << 16);
-                        need = !pair_prefilter_zero(C, sc, xa, vs_words[2 * a + 1], vs_words[2 * b + 1],
-                                                    h ? w.z : w.x);
                     }
-                    const unsigned m = __ballot_sync(FULL, need);
-                    if (need) {
+                }
+#pragma unroll
+                for (int i = 0; i < 2 * QG; ++i) {
+                    const unsigned m = __ballot_sync(FULL, need[i]);
+                    if (need[i]) {
                         const uint32_t idx = n_todo + __popc(m & ((1u << lane) - 1u));
-                        todo[3 * idx] = ab;
-                        todo[3 * idx + 1] = h ? w.z : w.x;
-                        todo[3 * idx + 2] = h ? w.w : w.y;
+                        const uint4 &wr = w[i / 2];
+                        todo[3 * idx] = abv[i];
+                        todo[3 * idx + 1] = (i & 1) ? wr.z : wr.x;
+                        todo[3 * idx + 2] = (i & 1) ? wr.w : wr.y;
                     }
                     n_todo += __popc(m);
                 }
@@ -864,6 +875,11 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                     const uint32_t ab = todo[3 * e];
                     a = ab & 0xFFFFu;
                     b = ab >> 16;
+                    if (xs[a] < xs[b]) { // j holds the larger multiplicity; ties keep the earlier
+                        const uint32_t tmp = a;
+                        a = b;
+                        b = tmp;
+                    }
                     wa = todo[3 * e + 1];
                     wb = todo[3 * e + 2];
                     gf = pair_gamma_filter(C, ratio_f, xs[a], vs_words[2 * a + 1], vs_words[2 * b + 1], wa);
