@@ -38,9 +38,11 @@ struct InstDev {
     uint32_t status; // bit 0: a bounded device wait gave up (reported as SDM_ETIMEOUT)
 };
 
-struct WorkItem {
+struct __align__(16) WorkItem {
     int32_t inst; // index into the batch's table of InstDev pointers
     int32_t cell; // cell within that run
+    int32_t off;  // the cell's first storage slot (the plan is rebuilt when the layout changes)
+    int32_t n;    // the cell's storage slots
 };
 
 // ---------------------------------------------------------------- Philox

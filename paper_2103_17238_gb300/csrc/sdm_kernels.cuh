@@ -219,13 +219,11 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
         const int sg = k % STAGES;
         const WorkItem it = items[i];
         const InstDev *P = insts[it.inst];
-        const int32_t off = P->cell_off[it.cell];
-        const int32_t n = P->cell_off[it.cell + 1] - off;
-        s_meta[sg] = make_int4(off, n, it.cell, it.inst);
+        s_meta[sg] = make_int4(it.off, it.n, it.cell, it.inst);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)n * 16u);
-        bulk_g2s(st_xi + sg * CAP, P->xi + off, (uint32_t)n * 8u, &s_bar[sg]);
-        bulk_g2s(st_v + sg * CAP, P->v + off, (uint32_t)n * 8u, &s_bar[sg]);
+        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)it.n * 16u);
+        bulk_g2s(st_xi + sg * CAP, P->xi + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
+        bulk_g2s(st_v + sg * CAP, P->v + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
     };
     if (t == 0)
         for (int k = 0; k < STAGES - 1; ++k)
@@ -585,20 +583,24 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
     }
     __syncwarp();
 
-    auto issue = [&](int k) { // lane 0: start loading this warp's k-th cell
+    // Lane 0 loads each work item one cell before it issues the item's
+    // copies, so that the item's load latency hides behind a cell's work.
+    WorkItem nxt{0, 0, 0, 0};
+    auto fetch = [&](int k) {
         const int i = gw + k * nw;
-        if (i >= n_items)
+        if (i < n_items)
+            nxt = items[i];
+    };
+    auto issue = [&](int k, const WorkItem &it) { // lane 0: start loading this warp's k-th cell
+        if (gw + k * nw >= n_items)
             return;
         const int sg = k % STAGES;
-        const WorkItem it = items[i];
         const InstDev *P = insts[it.inst];
-        const int32_t off = P->cell_off[it.cell];
-        const int32_t n = P->cell_off[it.cell + 1] - off;
-        s_meta[sg] = make_int4(off, n, it.cell, it.inst);
+        s_meta[sg] = make_int4(it.off, it.n, it.cell, it.inst);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)n * 16u);
-        bulk_g2s(st_xi + sg * CAP, P->xi + off, (uint32_t)n * 8u, &s_bar[sg]);
-        bulk_g2s(st_v + sg * CAP, P->v + off, (uint32_t)n * 8u, &s_bar[sg]);
+        mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)it.n * 16u);
+        bulk_g2s(st_xi + sg * CAP, P->xi + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
+        bulk_g2s(st_v + sg * CAP, P->v + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
     };
 
     auto flush = [&]() { // whole warp
@@ -625,13 +627,19 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
         __syncwarp();
     };
 
-    if (lane == 0)
-        for (int k = 0; k < STAGES - 1; ++k)
-            issue(k);
+    if (lane == 0) {
+        for (int k = 0; k < STAGES - 1; ++k) {
+            fetch(k);
+            issue(k, nxt);
+        }
+        fetch(STAGES - 1);
+    }
 
     for (int k = 0; gw + k * nw < n_items; ++k) {
-        if (lane == 0)
-            issue(k + STAGES - 1);
+        if (lane == 0) {
+            issue(k + STAGES - 1, nxt);
+            fetch(k + STAGES);
+        }
         const int sg = k % STAGES;
         const bool arrived = mbar_wait_bounded(&s_bar[sg], (uint32_t)(k / STAGES) & 1u);
         if (!__all_sync(FULL, arrived)) {

@@ -380,7 +380,7 @@ sdm_status build_plan(sdm_batch *b)
                 continue;
             const int cls = class_of(n, tun);
             if (cls >= 0) {
-                items[cls].push_back(WorkItem{i, cell});
+                items[cls].push_back(WorkItem{i, cell, c->h_cell_off[cell], n});
                 continue;
             }
             BigCell bc{};
