@@ -394,7 +394,8 @@ __device__ __forceinline__ float vt_guarded(const PairConsts &C, float r, bool &
 // the filter's error is below 2^-16.4 M (volumes 2^-20, radius 2^-18.8,
 // squares and fall speeds 2^-17.7, the difference absolute in M) and the
 // exact value's (binary64, or binary32 with a 1-ulp cube root) below
-// 2^-19 M.  So with E = 2^-10 M + 2^-100 and u in [u_lo, u_lo + 2^-23),
+// 2^-19 M: together below 2^-16.1 M.  So with E = 2^-13 M + 2^-100 (over 8
+// times that bound) and u in [u_lo, u_lo + 2^-23),
 // p - u lies in [pf - E - u_hi, pf + E - u_lo], and the bounds, widened by
 // the rounding of their own binary32 sums, pin ceil(p - u) when both fall in
 // one interval (m - 1, m].  The filter abstains within 2^-14 of a
@@ -426,7 +427,7 @@ __device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float 
         mag = (km * xjf) * sc;
         ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f);
     }
-    const float E = mag * 0x1p-10f + 0x1p-100f;
+    const float E = mag * 0x1p-13f + 0x1p-100f;
     const float slack = (fabsf(pf) + E + 1.0f) * 0x1p-20f;
     const float hi = ((pf + E) - u_lo) + slack;
     if (ok && hi <= 0.0f)

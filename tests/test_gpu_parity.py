@@ -90,6 +90,22 @@ def test_grid(env, kernel, precision):
     run.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "kfp32"])
+def test_grid_long_run(env, precision):
+    """600 steps of an 8 x 8 grid of the benchmark's cells: late in the run
+    the spectrum is broad, many pairs have p > 1 and their p - u falls near
+    an integer, so the binary32 filter decides close to its interval bound
+    and the exact path takes the pairs it leaves.  Bit for bit throughout."""
+    O, sdm, torch = env
+    g = I.grid_geometric(side=8, sd_per_cell=256, seed=0)
+    run = _gpu_run(sdm, "geometric", precision, g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 600, chunks=[150, 450])
+    xi, v = run.attributes()
+    st = _oracle_run(O, "geometric", precision, g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 600)
+    _assert_same(xi, v, st, f"grid 600 steps {precision}")
+    assert int((xi != g.xi).sum()) > g.n_sd // 2  # most SDs collided
+    run.close()
+
+
 RAGGED = [0, 1, 2, 3, 5, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 513, 1000, 2047, 2049,
           4095, 4096, 4097, 5000, 9001, 20001]
 
