@@ -262,7 +262,7 @@ sdm_status sdm_get_tuning(sdm_tuning *out);
  * owns every device buffer, a latency-bound loop that cannot afford an
  * allocator call.  It allocates nothing: no cudaMalloc, cudaFree or
  * allocating library routine.  Its scratch is one fixed array of device
- * memory inside the library (about 18 MiB for SDM_NOALLOC_MAX_SD SDs), which
+ * memory inside the library (about 8.6 MiB for SDM_NOALLOC_MAX_SD SDs), which
  * every GPU that loads the library holds until the process exits.
  *
  * One coalescence step (the same step as sdm_coalescence_step) of ONE cell

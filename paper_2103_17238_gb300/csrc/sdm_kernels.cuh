@@ -952,9 +952,9 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
 constexpr int kBigChunk = 8192;   // SDs per CTA in the histogram and scatter passes
 constexpr int kBigNT = 1024;
 constexpr int kBigMaxLB = 14;     // at most 16384 top-level buckets
-constexpr int kBucketCap = 2048;  // entries sorted in shared memory per bucket
+constexpr int kBucketCap = 1536;  // entries sorted in shared memory per bucket (1024 expected)
 constexpr int kBucketNT = 256;
-constexpr int kSubLB = 10;        // second-level buckets inside a bucket
+constexpr int kSubLB = 9;         // second-level buckets inside a bucket
 constexpr int kPairNT = 256;
 
 struct BigCell {
@@ -981,8 +981,7 @@ struct BigPairs {
 struct BigScratch {
     uint32_t *hist;     // per (chunk, bucket) counts, then prefixes
     uint32_t *bstart;   // bucket starts per cell, last entry = n_c
-    uint64_t *key;      // keys in bucket order
-    uint32_t *rank;     // ranks in bucket order
+    uint32_t *rank;     // ranks in bucket order (their keys are drawn again where needed)
     uint32_t *perm;     // ranks in sorted order
     double *scale;      // per big cell
     float *scale_f;
@@ -1102,28 +1101,37 @@ __global__ void __launch_bounds__(kBigNT) big_scatter_kernel(const BigChunk *__r
     const BigCell bc = bigs[ch.big];
     const InstDev *P = insts[bc.inst];
     const int NB = 1 << bc.lb;
+    // this chunk's first slot in every bucket
+    const uint32_t *h = S.hist + bc.hist_base + (int64_t)ch.chunk * NB;
+    const uint32_t *bs = S.bstart + bc.bkt_base;
     for (int i = threadIdx.x; i < NB; i += kBigNT)
-        s_cnt[i] = 0u;
+        s_cnt[i] = bs[i] + h[i];
     __syncthreads();
     const int64_t s = P->step + step_offset;
     const int64_t *gxi = P->xi + P->cell_off[bc.cell];
     const int sh = 64 - bc.lb;
-    const uint32_t *h = S.hist + bc.hist_base + (int64_t)ch.chunk * NB;
-    const uint32_t *bs = S.bstart + bc.bkt_base;
-    uint64_t *kout = S.key + bc.sd_base;
     uint32_t *rout = S.rank + bc.sd_base;
+    // only the rank is stored (4 bytes, not 12 with the key): the scattered
+    // writes then stay in L2 instead of costing partial-sector rewrites
     big_chunk_keys(P, bc, ch.chunk, s, gxi, [&](uint64_t k, uint32_t rank) {
-        const uint32_t b = (uint32_t)(k >> sh);
-        const uint32_t pos = bs[b] + h[b] + atomicAdd(&s_cnt[b], 1u);
-        kout[pos] = k;
-        rout[pos] = rank;
+        rout[atomicAdd(&s_cnt[(uint32_t)(k >> sh)], 1u)] = rank;
     });
 }
 
-// One CTA per top-level bucket: order its entries by (key, rank) through
-// second-level buckets on the next kSubLB key bits, write the ranks to perm.
+// The 64-bit sort key of the SD of rank r in a big cell (as big_chunk_keys).
+__device__ __forceinline__ uint64_t big_key(uint64_t seed, uint32_t cell, int64_t s, uint32_t r)
+{
+    const uint4 w = draw4(seed, r >> 1, cell, s, 0u);
+    return (r & 1u) ? (((uint64_t)w.z << 32) | w.w) : (((uint64_t)w.x << 32) | w.y);
+}
+
+// One CTA per top-level bucket: draw its entries' keys again, order them by
+// (key, rank) through second-level buckets on the next kSubLB key bits,
+// write the ranks to perm.
 __global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBucket *__restrict__ work,
-                                                                    const BigCell *__restrict__ bigs, BigScratch S)
+                                                                    const BigCell *__restrict__ bigs,
+                                                                    const InstDev *const *__restrict__ insts,
+                                                                    BigScratch S, int64_t step_offset)
 {
     constexpr int NSB = 1 << kSubLB;
     constexpr int R = kBucketCap / kBucketNT;
@@ -1136,19 +1144,22 @@ __global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBuc
     const uint32_t *bs = S.bstart + bc.bkt_base;
     const uint32_t lo = bs[bw.bucket], hi = bs[bw.bucket + 1];
     const uint32_t nb = hi - lo;
-    const uint64_t *kin = S.key + bc.sd_base + lo;
     const uint32_t *rin = S.rank + bc.sd_base + lo;
     uint32_t *pout = S.perm + bc.sd_base + lo;
     if (nb == 0)
         return;
+    const InstDev *P = insts[bc.inst];
+    const uint64_t seed = P->seed;
+    const int64_t s = P->step + step_offset;
+    const uint32_t cell = (uint32_t)bc.cell;
     if (nb > (uint32_t)kBucketCap) {
         // overfull bucket (never expected for uniform keys): rank by counting
         for (uint32_t e = threadIdx.x; e < nb; e += kBucketNT) {
-            const uint64_t k = kin[e];
             const uint32_t r = rin[e];
+            const uint64_t k = big_key(seed, cell, s, r);
             uint32_t cnt = 0;
             for (uint32_t m = 0; m < nb; ++m)
-                cnt += key_less(kin[m], rin[m], k, r) ? 1u : 0u;
+                cnt += key_less(big_key(seed, cell, s, rin[m]), rin[m], k, r) ? 1u : 0u;
             pout[cnt] = r;
         }
         return;
@@ -1164,8 +1175,8 @@ __global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBuc
         const uint32_t e = threadIdx.x + r * kBucketNT;
         slot[r] = 0xFFFFFFFFu;
         if (e < nb) {
-            key[r] = kin[e];
             rank[r] = rin[e];
+            key[r] = big_key(seed, cell, s, rank[r]);
             slot[r] = atomicAdd(&s_hist[(key[r] >> sh) & (NSB - 1)], 1u);
         }
     }

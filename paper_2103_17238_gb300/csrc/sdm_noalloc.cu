@@ -18,15 +18,14 @@
 namespace {
 
 constexpr int64_t kNaMaxSd = SDM_NOALLOC_MAX_SD;
-constexpr int kNaMaxLb = 12; // buckets for kNaMaxSd SDs (2^20 / 256)
+constexpr int kNaMaxLb = 10; // buckets for kNaMaxSd SDs (2^20 / 1024)
 constexpr int64_t kNaMaxChunks = (kNaMaxSd + kBigChunk - 1) / kBigChunk;
 constexpr int64_t kNaMaxPairBlocks = ((kNaMaxSd / 2 + 1) / 2 + kPairNT - 1) / kPairNT;
 
 constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the pieces inside the array.
-constexpr size_t kNaKey = 0;
-constexpr size_t kNaRank = na_align(kNaKey + 8 * (size_t)kNaMaxSd);
+constexpr size_t kNaRank = 0;
 constexpr size_t kNaPerm = na_align(kNaRank + 4 * (size_t)kNaMaxSd);
 constexpr size_t kNaHist = na_align(kNaPerm + 4 * (size_t)kNaMaxSd);
 constexpr size_t kNaBstart = na_align(kNaHist + 4 * (size_t)kNaMaxChunks * ((size_t)1 << kNaMaxLb));
@@ -41,7 +40,7 @@ constexpr size_t kNaInsts = na_align(kNaInst + sizeof(InstDev));
 constexpr size_t kNaCellOff = na_align(kNaInsts + sizeof(InstDev *));
 constexpr size_t kNaBytes = na_align(kNaCellOff + 2 * sizeof(int32_t));
 
-// About 18 MiB; every GPU that loads the library holds it until exit.
+// About 8.6 MiB; every GPU that loads the library holds it until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 // Fills the run record, the one-cell descriptor and the work lists in the
@@ -160,13 +159,14 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     inst.n_cells = 1;
     const int n = (int)n_sd;
     const int lb = big_lb(n);
+    if (lb > kNaMaxLb) // cannot happen for n <= kNaMaxSd; the tables are sized for kNaMaxLb
+        return fail(nullptr, SDM_EINVAL, "sdm_cell_step_noalloc: %d buckets exceed the static tables", 1 << lb);
     const int n_chunks = (n + kBigChunk - 1) / kBigChunk;
     const int n_pair_blocks = ((n / 2 + 1) / 2 + kPairNT - 1) / kPairNT;
     noalloc_setup_kernel<<<16, 256, 0, s>>>(base, inst, n, lb, n_chunks, n_pair_blocks);
     BigScratch S;
     S.hist = reinterpret_cast<uint32_t *>(base + kNaHist);
     S.bstart = reinterpret_cast<uint32_t *>(base + kNaBstart);
-    S.key = reinterpret_cast<uint64_t *>(base + kNaKey);
     S.rank = reinterpret_cast<uint32_t *>(base + kNaRank);
     S.perm = reinterpret_cast<uint32_t *>(base + kNaPerm);
     S.scale = reinterpret_cast<double *>(base + kNaScale);
@@ -182,7 +182,7 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     big_colscan_kernel<<<tiles, kBigColNT, 0, s>>>(big, tiles, S);
     big_scan_kernel<<<1, kBigNT, big_hist_smem(kBigMaxLB), s>>>(big, insts, S);
     big_scatter_kernel<<<n_chunks, kBigNT, hs, s>>>(chunks, big, insts, S, 0);
-    big_bucket_sort_kernel<<<1 << lb, kBucketNT, 0, s>>>(buckets, big, S);
+    big_bucket_sort_kernel<<<1 << lb, kBucketNT, 0, s>>>(buckets, big, insts, S, 0);
     big_pairs_kernel<<<n_pair_blocks, kPairNT, 0, s>>>(pairs, big, insts, S, 0);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)

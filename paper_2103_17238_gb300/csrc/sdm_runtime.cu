@@ -201,7 +201,7 @@ int big_lb(int n)
     int lg = 0;
     while ((1 << lg) < n)
         ++lg;
-    return std::min(std::max(lg - 8, 1), kBigMaxLB);
+    return std::min(std::max(lg - 10, 1), kBigMaxLB);
 }
 
 size_t big_hist_smem(int lb) { return (size_t)sizeof(uint32_t) << lb; }
@@ -455,12 +455,11 @@ sdm_status build_plan(sdm_batch *b)
         pl.d_pairs = reinterpret_cast<BigPairs *>(d + off_pairs);
         pl.scratch.hist = plan_alloc<uint32_t>(pl, mem, hist_total);
         pl.scratch.bstart = plan_alloc<uint32_t>(pl, mem, bkt_total);
-        pl.scratch.key = plan_alloc<uint64_t>(pl, mem, sd_total);
         pl.scratch.rank = plan_alloc<uint32_t>(pl, mem, sd_total);
         pl.scratch.perm = plan_alloc<uint32_t>(pl, mem, sd_total);
         pl.scratch.scale = plan_alloc<double>(pl, mem, bigs.size());
         pl.scratch.scale_f = plan_alloc<float>(pl, mem, bigs.size());
-        if (!pl.scratch.hist || !pl.scratch.bstart || !pl.scratch.key || !pl.scratch.rank || !pl.scratch.perm ||
+        if (!pl.scratch.hist || !pl.scratch.bstart || !pl.scratch.rank || !pl.scratch.perm ||
             !pl.scratch.scale || !pl.scratch.scale_f)
             return fail(&b->error, SDM_ENOMEM, "batch plan: big-cell scratch allocation failed");
     }
@@ -484,7 +483,8 @@ void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
         big_colscan_kernel<<<pl.n_big * tiles, kBigColNT, 0, st>>>(pl.d_bigs, tiles, pl.scratch);
         big_scan_kernel<<<pl.n_big, kBigNT, big_hist_smem(kBigMaxLB), st>>>(pl.d_bigs, pl.d_insts, pl.scratch);
         big_scatter_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
-        big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.scratch);
+        big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.d_insts, pl.scratch,
+                                                                   off);
         big_pairs_kernel<<<pl.n_pair_blocks, kPairNT, 0, st>>>(pl.d_pairs, pl.d_bigs, pl.d_insts, pl.scratch, off);
     }
 }
