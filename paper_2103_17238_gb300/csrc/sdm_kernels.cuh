@@ -992,15 +992,26 @@ template <typename F>
 __device__ __forceinline__ void big_chunk_keys(const InstDev *P, const BigCell &bc, int chunk, int64_t s,
                                                const int64_t *gxi, F &&f)
 {
+    constexpr int QPT = kBigChunk / 2 / kBigNT; // SD pairs per thread
+    static_assert(QPT * kBigNT * 2 == kBigChunk, "chunk = threads x pairs");
     const int lo2 = (chunk * kBigChunk) / 2;
     const int hi2 = min((chunk + 1) * kBigChunk, bc.n) / 2;
-    for (int q = lo2 + (int)threadIdx.x; q < hi2; q += kBigNT) {
-        const longlong2 x = reinterpret_cast<const longlong2 *>(gxi)[q];
-        if ((x.x > 0) | (x.y > 0)) {
-            const uint4 w = draw4(P->seed, (uint32_t)q, (uint32_t)bc.cell, s, 0u);
-            if (x.x > 0)
+    // every load of the thread first, so that they are in flight together
+    longlong2 x[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) {
+        const int q = lo2 + (int)threadIdx.x + i * kBigNT;
+        x[i] = q < hi2 ? reinterpret_cast<const longlong2 *>(gxi)[q] : make_longlong2(0, 0);
+    }
+    const uint64_t seed = P->seed;
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) {
+        const int q = lo2 + (int)threadIdx.x + i * kBigNT;
+        if ((x[i].x > 0) | (x[i].y > 0)) {
+            const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)bc.cell, s, 0u);
+            if (x[i].x > 0)
                 f(((uint64_t)w.x << 32) | w.y, (uint32_t)(2 * q));
-            if (x.y > 0)
+            if (x[i].y > 0)
                 f(((uint64_t)w.z << 32) | w.w, (uint32_t)(2 * q + 1));
         }
     }
@@ -1226,22 +1237,50 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
     const uint32_t *perm = S.perm + bc.sd_base;
     const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
     const uint4 w = draw4(P->seed, q, (uint32_t)bc.cell, s, 1u);
+    // both pairs' SDs are gathered at once (eight independent loads)
+    uint32_t A[2], B[2];
+    int64_t XA[2], XB[2];
+    double VA[2], VB[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t l = 2 * q + h;
+        A[h] = B[h] = 0;
+        if (l < n_pairs) {
+            const uint2 ab = reinterpret_cast<const uint2 *>(perm)[l];
+            A[h] = ab.x;
+            B[h] = ab.y;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        XA[h] = XB[h] = 0;
+        VA[h] = VB[h] = 0.0;
+        if (2 * q + h < n_pairs) {
+            XA[h] = gxi[A[h]];
+            XB[h] = gxi[B[h]];
+            VA[h] = gv[A[h]];
+            VB[h] = gv[B[h]];
+        }
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const uint32_t l = 2 * q + h;
         if (l >= n_pairs)
             break;
-        uint32_t a = perm[2 * l], b = perm[2 * l + 1];
-        int64_t xa = gxi[a], xb = gxi[b];
-        if (xa < xb) {
+        uint32_t a = A[h], b = B[h];
+        int64_t xa = XA[h], xb = XB[h];
+        double va = VA[h], vb = VB[h];
+        if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
             const uint32_t tmp = a;
             a = b;
             b = tmp;
             const int64_t tx = xa;
             xa = xb;
             xb = tx;
+            const double tv = va;
+            va = vb;
+            vb = tv;
         }
-        double va = gv[a], vb = gv[b];
         const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
         const int32_t gf = pair_gamma_filter(C, ratio_f, xa, va, vb, wa);
         if (gf == 0)
