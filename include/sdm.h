@@ -294,6 +294,36 @@ sdm_status sdm_get_tuning(sdm_tuning *out);
 sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step, int64_t *xi, double *volume, int64_t n_sd,
                                  void *cuda_stream);
 
+/* ---- diagnostics.  Not a product of the paper: the sums its coalescence
+ * must keep.  Shima's update (the fourth part of the step) moves volume
+ * between the two SDs of a pair and never adds multiplicity, so the total
+ * water volume sum(xi v) is conserved (up to binary64 rounding) and the
+ * total multiplicity sum(xi) never increases. */
+typedef struct sdm_diag {
+    int64_t live_sd;    /* SDs inside the domain (cell >= 0) with xi > 0 */
+    uint64_t sum_xi_lo; /* sum of their xi, exact as a 128-bit integer: low 64 bits */
+    uint64_t sum_xi_hi; /*   and high 64 bits */
+    double sum_xi_v;    /* sum of their xi v, m^3, in binary64: each product added with one
+                           rounding, in a fixed order, so repeated calls give the same bits */
+} sdm_diag;
+
+/* The sums over the context's current state, computed on its stream; the
+ * call waits for them.  Errors: SDM_EINVAL (NULL out), SDM_ESTATE (no
+ * attributes yet, or an unusable context), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_diagnostics(sdm_ctx *ctx, sdm_diag *out);
+
+/* Self-test of failure detection on the device, without a fault.  Every
+ * device-side wait of the step (for a bulk copy to arrive) is bounded: a
+ * wait that gives up makes the kernel record it in the run's status word and
+ * return, and the host reports SDM_ETIMEOUT.  This call runs that path on its
+ * own: one block on cuda_stream (NULL: the legacy default stream) waits on a
+ * barrier that nothing completes and gives up after max_polls polls (1 ..
+ * 2^24).  It returns SDM_ETIMEOUT when the wait gave up as designed (the
+ * expected result; the device stays usable), SDM_ESTATE if the barrier
+ * completed, SDM_EINVAL for max_polls out of range, SDM_ENOMEM or SDM_ECUDA.
+ * Messages from sdm_last_error(NULL). */
+sdm_status sdm_selftest_bounded_wait(void *cuda_stream, int64_t max_polls);
+
 #ifdef __cplusplus
 }
 #endif

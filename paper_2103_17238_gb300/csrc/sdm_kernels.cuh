@@ -115,12 +115,26 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 // Bounded wait on an mbarrier phase: ~2^22 polls (each poll may suspend the
 // thread for a hardware-defined interval), then give up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t max_polls = 1u << 22)
 {
-    for (uint32_t it = 0; it < (1u << 22); ++it)
+    for (uint32_t it = 0; it < max_polls; ++it)
         if (mbar_try_wait(bar, parity))
             return true;
     return false;
+}
+
+// The bounded-wait path on its own: a barrier that expects two arrivals gets
+// one, so its phase never completes; lane 0 waits at most max_polls polls
+// and records whether it gave up (1) or saw the phase complete (0).
+__global__ void selftest_wait_kernel(uint32_t max_polls, uint32_t *out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+        out[0] = mbar_wait_bounded(&bar, 0u, max_polls) ? 0u : 1u;
+    }
 }
 
 // -------------------------------------------------------------- cell step
@@ -1305,6 +1319,90 @@ __global__ void advance_steps_kernel(InstDev *const *insts, int32_t n_inst, int6
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_inst)
         insts[i]->step += delta ? delta[i] : n;
+}
+
+// ------------------------------------------------------------ diagnostics
+// Conservation sums of the SDs inside the domain (slots [0, n_in)): live
+// count, sum of xi (128-bit, exact) and sum of xi v (binary64).  Each thread
+// adds its slots in index order, then warps and blocks combine in a fixed
+// tree, so that a given grid gives the same bits every time.
+struct DiagPart {
+    unsigned long long live, xi_lo, xi_hi;
+    double xv;
+};
+constexpr int kDiagNT = 256;
+
+__device__ __forceinline__ void add128(unsigned long long &lo, unsigned long long &hi, unsigned long long blo,
+                                       unsigned long long bhi)
+{
+    const unsigned long long s = lo + blo;
+    hi += bhi + (s < lo ? 1ull : 0ull);
+    lo = s;
+}
+
+__device__ __forceinline__ void diag_combine(DiagPart &a, const DiagPart &b)
+{
+    a.live += b.live;
+    add128(a.xi_lo, a.xi_hi, b.xi_lo, b.xi_hi);
+    a.xv = __dadd_rn(a.xv, b.xv);
+}
+
+__device__ __forceinline__ DiagPart diag_shfl_down(const DiagPart &a, int d)
+{
+    DiagPart b;
+    b.live = __shfl_down_sync(0xFFFFFFFFu, a.live, d);
+    b.xi_lo = __shfl_down_sync(0xFFFFFFFFu, a.xi_lo, d);
+    b.xi_hi = __shfl_down_sync(0xFFFFFFFFu, a.xi_hi, d);
+    b.xv = __shfl_down_sync(0xFFFFFFFFu, a.xv, d);
+    return b;
+}
+
+// fixed tree over the block: lanes within warps, then warps (thread 0 ends with the block's sum)
+__device__ __forceinline__ DiagPart diag_block_reduce(DiagPart a)
+{
+    __shared__ DiagPart s_w[kDiagNT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const DiagPart b = diag_shfl_down(a, d);
+        diag_combine(a, b);
+    }
+    if (lane == 0)
+        s_w[warp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kDiagNT / 32; ++w)
+            diag_combine(a, s_w[w]);
+    return a;
+}
+
+__global__ void __launch_bounds__(kDiagNT) diag_partial_kernel(const InstDev *__restrict__ P, int64_t n_in,
+                                                               DiagPart *__restrict__ parts)
+{
+    DiagPart a{0ull, 0ull, 0ull, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * kDiagNT;
+    for (int64_t i = (int64_t)blockIdx.x * kDiagNT + threadIdx.x; i < n_in; i += stride) {
+        const int64_t x = P->xi[i];
+        if (x > 0) {
+            a.live += 1ull;
+            add128(a.xi_lo, a.xi_hi, (unsigned long long)x, 0ull);
+            a.xv = __fma_rn(xi2d(x), P->v[i], a.xv);
+        }
+    }
+    a = diag_block_reduce(a);
+    if (threadIdx.x == 0)
+        parts[blockIdx.x] = a;
+}
+
+__global__ void __launch_bounds__(kDiagNT) diag_final_kernel(const DiagPart *__restrict__ parts, int32_t n_parts,
+                                                             DiagPart *__restrict__ out)
+{
+    DiagPart a{0ull, 0ull, 0ull, 0.0};
+    for (int i = threadIdx.x; i < n_parts; i += kDiagNT)
+        diag_combine(a, parts[i]);
+    a = diag_block_reduce(a);
+    if (threadIdx.x == 0)
+        *out = a;
 }
 
 // -------------------------------------------------------------- spectrum

@@ -115,6 +115,7 @@ sdm_status noalloc_base(unsigned char **out)
 extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step, int64_t *xi, double *volume,
                                             int64_t n_sd, void *cuda_stream)
 {
+    NvtxRange nvtx_range("sdm_cell_step_noalloc");
     sdm_status st = check_config(cfg, nullptr);
     if (st != SDM_OK)
         return st;

@@ -3,6 +3,7 @@
 // CUDA-graph replay, the spectrum product.  Declarations and the contract of
 // every call are in include/sdm.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +22,15 @@ using namespace sdm;
 namespace {
 
 thread_local std::string g_thread_error;
+
+// An NVTX range around each C-ABI call (a profiler's timeline shows the
+// calls; without an attached tool a push or pop costs a few nanoseconds).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct DevMem {
     sdm_alloc_fn fn = nullptr;
@@ -765,6 +775,7 @@ int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t larges
 
 sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_stream, sdm_ctx **out)
 {
+    NvtxRange nvtx_range("sdm_create");
     if (!out)
         return fail(nullptr, SDM_EINVAL, "out is NULL");
     sdm_status st = check_config(cfg, nullptr);
@@ -801,6 +812,7 @@ sdm_status sdm_create(const sdm_config *cfg, int64_t capacity_sd, void *cuda_str
 sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, const double *volume,
                               const int32_t *cell_id, int on_device)
 {
+    NvtxRange nvtx_range("sdm_set_attributes");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -946,6 +958,7 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
 
 sdm_status sdm_coalescence_step(sdm_ctx *ctx, int32_t n_steps)
 {
+    NvtxRange nvtx_range("sdm_coalescence_step");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -976,6 +989,7 @@ sdm_status sdm_coalescence_step(sdm_ctx *ctx, int32_t n_steps)
 sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, int per_cell, double *out,
                         int out_on_device)
 {
+    NvtxRange nvtx_range("sdm_spectrum");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -1031,6 +1045,7 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
 
 sdm_status sdm_get_attributes(sdm_ctx *ctx, int64_t *xi, double *volume, int on_device)
 {
+    NvtxRange nvtx_range("sdm_get_attributes");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -1076,6 +1091,7 @@ sdm_status sdm_get_info(const sdm_ctx *ctx, sdm_info *out)
 
 sdm_status sdm_destroy(sdm_ctx *ctx)
 {
+    NvtxRange nvtx_range("sdm_destroy");
     if (!ctx)
         return SDM_OK;
     if (ctx->self_batch) {
@@ -1105,6 +1121,7 @@ const char *sdm_last_error(const sdm_ctx *ctx)
 sdm_status sdm_batch_create(sdm_ctx *const *ctxs, int32_t n_ctx, void *cuda_stream, int32_t use_graph,
                             int32_t graph_steps, sdm_batch **out)
 {
+    NvtxRange nvtx_range("sdm_batch_create");
     if (!out || !ctxs || n_ctx < 1)
         return fail(nullptr, SDM_EINVAL, "need out, ctxs and n_ctx >= 1");
     sdm_batch *b = new (std::nothrow) sdm_batch();
@@ -1123,6 +1140,7 @@ sdm_status sdm_batch_create(sdm_ctx *const *ctxs, int32_t n_ctx, void *cuda_stre
 
 sdm_status sdm_batch_step(sdm_batch *batch, int32_t n_steps)
 {
+    NvtxRange nvtx_range("sdm_batch_step");
     if (!batch)
         return fail(nullptr, SDM_EINVAL, "batch is NULL");
     return batch_step(batch, n_steps);
@@ -1130,6 +1148,7 @@ sdm_status sdm_batch_step(sdm_batch *batch, int32_t n_steps)
 
 sdm_status sdm_batch_destroy(sdm_batch *batch)
 {
+    NvtxRange nvtx_range("sdm_batch_destroy");
     if (!batch)
         return SDM_OK;
     batch_release(batch);
@@ -1166,6 +1185,67 @@ sdm_status sdm_get_tuning(sdm_tuning *out)
         return fail(nullptr, SDM_EINVAL, "out is NULL");
     *out = current_tuning();
     return SDM_OK;
+}
+
+sdm_status sdm_diagnostics(sdm_ctx *ctx, sdm_diag *out)
+{
+    NvtxRange nvtx_range("sdm_diagnostics");
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!out)
+        return fail(&ctx->error, SDM_EINVAL, "out is NULL");
+    if (!ctx->has_attributes)
+        return fail(&ctx->error, SDM_ESTATE, "no attributes set");
+    const int64_t n_in = ctx->h_cell_off[ctx->cfg.n_cells]; // slots of the cells (not the SDs outside)
+    // the grid depends on the size only: the same state gives the same bits
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1216, (n_in + kDiagNT * 8 - 1) / (kDiagNT * 8)));
+    const size_t bytes = sizeof(DiagPart) * ((size_t)blocks + 1);
+    DiagPart *d = (DiagPart *)ctx->mem.get(bytes);
+    if (!d)
+        return fail(&ctx->error, SDM_ENOMEM, "diagnostics scratch allocation failed");
+    cudaStream_t s = ctx->stream;
+    diag_partial_kernel<<<blocks, kDiagNT, 0, s>>>(ctx->d_inst, n_in, d);
+    diag_final_kernel<<<1, kDiagNT, 0, s>>>(d, blocks, d + blocks);
+    DiagPart h{};
+    CTX_CUDA(ctx, cudaGetLastError());
+    CTX_CUDA(ctx, cudaMemcpyAsync(&h, d + blocks, sizeof h, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->mem.put(d, bytes);
+    out->live_sd = (int64_t)h.live;
+    out->sum_xi_lo = h.xi_lo;
+    out->sum_xi_hi = h.xi_hi;
+    out->sum_xi_v = h.xv;
+    return SDM_OK;
+}
+
+sdm_status sdm_selftest_bounded_wait(void *cuda_stream, int64_t max_polls)
+{
+    NvtxRange nvtx_range("sdm_selftest_bounded_wait");
+    if (max_polls < 1 || max_polls > (int64_t)1 << 24)
+        return fail(nullptr, SDM_EINVAL, "max_polls = %lld outside [1, 2^24]", (long long)max_polls);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    uint32_t *d = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&d, sizeof(uint32_t), s);
+    if (e != cudaSuccess)
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? SDM_ENOMEM : SDM_ECUDA, "self-test allocation: %s",
+                    cudaGetErrorString(e));
+    uint32_t h = 0;
+    selftest_wait_kernel<<<1, 32, 0, s>>>((uint32_t)max_polls, d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    if (e == cudaSuccess)
+        e = ef;
+    if (e != cudaSuccess)
+        return fail(nullptr, SDM_ECUDA, "self-test: %s", cudaGetErrorString(e));
+    if (h == 1u)
+        return fail(nullptr, SDM_ETIMEOUT, "the bounded wait gave up after %lld polls, as designed",
+                    (long long)max_polls);
+    return fail(nullptr, SDM_ESTATE, "the self-test barrier completed, which it never should");
 }
 
 const char *sdm_batch_last_error(const sdm_batch *batch)

@@ -505,6 +505,7 @@ int sed_grid(int32_t n_groups)
 
 extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device)
 {
+    NvtxRange nvtx_range("sdm_set_positions");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -552,6 +553,7 @@ extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t n
 
 extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
 {
+    NvtxRange nvtx_range("sdm_sedimentation_step");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -627,6 +629,7 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
 
 extern "C" sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, int on_device)
 {
+    NvtxRange nvtx_range("sdm_get_positions");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;

@@ -31,6 +31,7 @@ EXPORTS = [
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
     "sdm_cell_step_noalloc", "sdm_set_tuning", "sdm_get_tuning",
     "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions",
+    "sdm_diagnostics", "sdm_selftest_bounded_wait",
 ]
 NOALLOC_MAX_SD = 1 << 20
 
@@ -87,6 +88,15 @@ class sdm_info(ctypes.Structure):
     ]
 
 
+class sdm_diag(ctypes.Structure):
+    _fields_ = [
+        ("live_sd", ctypes.c_int64),
+        ("sum_xi_lo", ctypes.c_uint64),
+        ("sum_xi_hi", ctypes.c_uint64),
+        ("sum_xi_v", ctypes.c_double),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -127,10 +137,13 @@ def load(path: str = LIB_PATH):
         L.sdm_sedimentation_step.argtypes = [vp, P(ctypes.c_double)]
         L.sdm_get_positions.argtypes = [vp, vp, vp, ctypes.c_int]
         L.sdm_get_tuning.argtypes = [P(sdm_tuning)]
+        L.sdm_diagnostics.argtypes = [vp, P(sdm_diag)]
+        L.sdm_selftest_bounded_wait.argtypes = [vp, i64]
         for name in ("sdm_create", "sdm_set_attributes", "sdm_coalescence_step", "sdm_spectrum",
                      "sdm_get_attributes", "sdm_get_info", "sdm_destroy", "sdm_batch_create",
                      "sdm_batch_step", "sdm_batch_destroy", "sdm_cell_step_noalloc", "sdm_set_tuning",
-                     "sdm_get_tuning", "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions"):
+                     "sdm_get_tuning", "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions",
+                     "sdm_diagnostics", "sdm_selftest_bounded_wait"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -261,6 +274,22 @@ def sdm_get_info(ctx) -> sdm_info:
     info = sdm_info()
     _check(load().sdm_get_info(ctx, ctypes.byref(info)), "sdm_get_info", ctx)
     return info
+
+
+def sdm_diagnostics(ctx) -> dict:
+    """Conservation sums of the current state: live SDs, sum of xi (exact
+    int), sum of xi v (m^3)."""
+    d = sdm_diag()
+    _check(load().sdm_diagnostics(ctx, ctypes.byref(d)), "sdm_diagnostics", ctx=ctx)
+    return {"live_sd": int(d.live_sd), "sum_xi": (int(d.sum_xi_hi) << 64) | int(d.sum_xi_lo),
+            "sum_xi_v": float(d.sum_xi_v)}
+
+
+def sdm_selftest_bounded_wait(max_polls: int, stream: int = 0) -> int:
+    """Runs the device's bounded-wait path on a barrier nothing completes;
+    returns the status (SDM_ETIMEOUT is the expected, healthy result)."""
+    st = load().sdm_selftest_bounded_wait(ctypes.c_void_p(stream or None), int(max_polls))
+    return int(st)
 
 
 def sdm_footprint_bytes(capacity_sd: int, n_cells: int, largest_cell: int) -> int:
@@ -404,6 +433,9 @@ class Run:
 
     def info(self) -> sdm_info:
         return sdm_get_info(self.h)
+
+    def diagnostics(self) -> dict:
+        return sdm_diagnostics(self.h)
 
     def close(self):
         if self.h:

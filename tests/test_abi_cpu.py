@@ -49,7 +49,7 @@ def test_ctypes_layout_matches_the_header(tmp_path):
     from paper_2103_17238_gb300 import sdm
 
     prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "sdm.h"', 'int main(void){']
-    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning):
+    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning, sdm.sdm_diag):
         name = st.__name__
         prog.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for f, _ in st._fields_:
@@ -61,7 +61,7 @@ def test_ctypes_layout_matches_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
                                                        check=True).stdout.splitlines())
-    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning):
+    for st in (sdm.sdm_config, sdm.sdm_info, sdm.sdm_tuning, sdm.sdm_diag):
         assert int(out[st.__name__]) == ctypes.sizeof(st)
         for f, _ in st._fields_:
             assert int(out[f"{st.__name__}.{f}"]) == getattr(st, f).offset, f
@@ -146,3 +146,18 @@ def test_autotune_candidates_are_valid_and_signature_is_stable(lib):
     b = autotune.signature([FakeRun("golovin", 1100, 250), FakeRun("geometric", 60, 2900)])
     c = autotune.signature([FakeRun("golovin", 1000, 600)])
     assert a == b and a != c
+
+
+def test_selftest_rejects_bad_poll_counts_before_touching_the_gpu(lib):
+    from paper_2103_17238_gb300 import sdm
+
+    for polls in (0, -5, (1 << 24) + 1):
+        assert sdm.sdm_selftest_bounded_wait(polls) == sdm.SDM_EINVAL
+        assert b"max_polls" in lib.sdm_last_error(None)
+
+
+def test_diagnostics_rejects_null_context(lib):
+    from paper_2103_17238_gb300 import sdm
+
+    d = sdm.sdm_diag()
+    assert lib.sdm_diagnostics(None, ctypes.byref(d)) == sdm.SDM_EINVAL
