@@ -55,15 +55,24 @@ L2_FLUSH_BYTES = 256 << 20
 EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "serving", "sedimentation")
 
 
-KERNEL_SOURCES = ("sdm_device.cuh", "sdm_kernels.cuh")  # the step kernel and every helper it uses
+# The step kernel and every helper it uses: the device header, and the kernel
+# file up to the end of the warp-per-cell kernel (the large-cell path, the
+# spectrum and the diagnostics follow it and do not change it).
+KERNEL_SOURCES = (("sdm_device.cuh", None), ("sdm_kernels.cuh", b"// ----------------------------------------------------------- big cells"))
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_17238_gb300", "csrc")
-    for f in KERNEL_SOURCES:
+    for f, end in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+            text = fh.read()
+        if end is not None:
+            cut = text.find(end)
+            if cut < 0:
+                raise RuntimeError(f"{f}: end marker of the hashed region is missing")
+            text = text[:cut]
+        h.update(text)
     return h.hexdigest()[:16]
 
 
