@@ -1561,13 +1561,20 @@ __global__ void __launch_bounds__(kSpecTotNT) spectrum_total_kernel(const InstDe
         }
     }
     __syncthreads();
+    // Bins that no thread of the block touched hold zeros only: they skip the
+    // binary64 adds (adding +0.0 changes no sum, so the result is the same).
     for (int b = warp; b < nb; b += kSpecTotNT / 32) {
-        double sum = 0.0;
+        bool any = false;
         for (int j = lane; j < kSpecTotNT; j += 32)
-            sum = __dadd_rn(sum, s_col[b * kSpecTotNT + j]);
+            any |= s_col[b * kSpecTotNT + j] != 0.0;
+        double sum = 0.0;
+        if (__any_sync(0xFFFFFFFFu, any)) {
+            for (int j = lane; j < kSpecTotNT; j += 32)
+                sum = __dadd_rn(sum, s_col[b * kSpecTotNT + j]);
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1)
-            sum = __dadd_rn(sum, __shfl_down_sync(0xFFFFFFFFu, sum, d));
+            for (int d = 16; d > 0; d >>= 1)
+                sum = __dadd_rn(sum, __shfl_down_sync(0xFFFFFFFFu, sum, d));
+        }
         if (lane == 0)
             partial[(int64_t)b * gridDim.x + blockIdx.x] = sum;
     }
