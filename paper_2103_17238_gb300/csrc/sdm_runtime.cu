@@ -37,11 +37,21 @@ struct DevMem {
     sdm_free_fn ffn = nullptr;
     void *user = nullptr;
     cudaStream_t stream = nullptr;
+    // Small blocks (per-call scratch: validation counts, offsets, spectrum
+    // partials) are kept for the next call instead of going back through the
+    // allocator hook each time.  Every use is ordered on this stream, so a
+    // block handed out again follows its last use.
+    static constexpr size_t kKeepMax = (size_t)1 << 19; // bytes
+    static constexpr size_t kKeepBlocks = 6;
+    struct Block {
+        void *p;
+        size_t bytes;
+    };
+    std::vector<Block> kept; // free blocks
+    std::vector<Block> lent; // kept-size blocks in use (their true sizes)
 
-    void *get(size_t bytes)
+    void *raw_get(size_t bytes)
     {
-        if (bytes == 0)
-            bytes = 16;
         if (fn)
             return fn(bytes, (void *)stream, user);
         void *p = nullptr;
@@ -51,14 +61,69 @@ struct DevMem {
         }
         return p;
     }
-    void put(void *p, size_t bytes)
+    void raw_put(void *p, size_t bytes)
     {
-        if (!p)
-            return;
         if (ffn)
             ffn(p, bytes, (void *)stream, user);
         else
             cudaFreeAsync(p, stream);
+    }
+    void *get(size_t bytes)
+    {
+        if (bytes == 0)
+            bytes = 16;
+        if (bytes > kKeepMax)
+            return raw_get(bytes);
+        size_t best = kept.size();
+        for (size_t i = 0; i < kept.size(); ++i)
+            if (kept[i].bytes >= bytes && (best == kept.size() || kept[i].bytes < kept[best].bytes))
+                best = i;
+        Block b;
+        if (best < kept.size()) {
+            b = kept[best];
+            kept.erase(kept.begin() + (std::ptrdiff_t)best);
+        } else {
+            b.bytes = bytes;
+            b.p = raw_get(bytes);
+            if (!b.p)
+                return nullptr;
+        }
+        lent.push_back(b);
+        return b.p;
+    }
+    void put(void *p, size_t bytes)
+    {
+        if (!p)
+            return;
+        for (size_t i = 0; i < lent.size(); ++i)
+            if (lent[i].p == p) {
+                const Block b = lent[i];
+                lent.erase(lent.begin() + (std::ptrdiff_t)i);
+                if (kept.size() < kKeepBlocks)
+                    kept.push_back(b);
+                else
+                    raw_put(b.p, b.bytes);
+                return;
+            }
+        raw_put(p, bytes);
+    }
+    DevMem() = default;
+    // The block lists belong to one owner: a second owner takes the hooks only.
+    DevMem(const DevMem &) = delete;
+    DevMem &operator=(const DevMem &) = delete;
+    void use_hooks_of(const DevMem &o, cudaStream_t s)
+    {
+        fn = o.fn;
+        ffn = o.ffn;
+        user = o.user;
+        stream = s;
+    }
+    // returns the kept blocks to the allocator (before the owner goes away)
+    void release_kept()
+    {
+        for (const Block &b : kept)
+            raw_put(b.p, b.bytes);
+        kept.clear();
     }
 };
 
@@ -542,8 +607,7 @@ sdm_status batch_init(sdm_batch *b, sdm_ctx *const *ctxs, int32_t n_ctx, cudaStr
         b->versions.push_back(ctxs[i]->layout_version);
     }
     b->stream = stream;
-    b->mem = ctxs[0]->mem;
-    b->mem.stream = stream;
+    b->mem.use_hooks_of(ctxs[0]->mem, stream);
     b->use_graph = use_graph != 0;
     b->graph_steps = graph_steps > 0 ? graph_steps : 16;
     cudaError_t e = configure_kernels_once();
@@ -568,6 +632,7 @@ void batch_release(sdm_batch *b)
     b->graph_exec = nullptr;
     b->capture_stream = nullptr;
     plan_free(b->plan, b->mem);
+    b->mem.release_kept();
 }
 
 sdm_status batch_step(sdm_batch *b, int32_t n_steps)
@@ -764,11 +829,13 @@ int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t larges
 {
     const int64_t slots = capacity_sd + n_cells + 1;
     int64_t bytes = slots * (8 + 8 + 4) + ((int64_t)n_cells + 2) * 4 + (int64_t)sizeof(InstDev);
+    // small per-call scratch kept between calls, by the context and by its own batch
+    bytes += 2 * (int64_t)(DevMem::kKeepBlocks * DevMem::kKeepMax);
     if (largest_cell > current_tuning().smem_max_sd) {
-        // big-cell scratch, at most: keys, ranks, perm per SD; counts per chunk and bucket
+        // big-cell scratch, at most: rank and perm per SD; counts per chunk and bucket
         const int lb = big_lb(largest_cell);
         const int64_t chunks = (capacity_sd + kBigChunk - 1) / kBigChunk + n_cells;
-        bytes += capacity_sd * (8 + 4 + 4) + (chunks << lb) * 4 + ((int64_t)n_cells << lb) * 4;
+        bytes += capacity_sd * (4 + 4) + (chunks << lb) * 4 + ((int64_t)n_cells << lb) * 4;
     }
     return bytes;
 }
@@ -1104,6 +1171,7 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     ctx->mem.put(ctx->d_cell_off, 0);
     ctx->mem.put(ctx->d_inst, 0);
     sed_release(ctx);
+    ctx->mem.release_kept();
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     delete ctx;
     if (e != cudaSuccess)

@@ -88,7 +88,7 @@ def test_destroy_null_and_footprint(lib):
     small = sdm.sdm_footprint_bytes(4096, 1, 4096)
     assert small == (4096 + 1) * 20 + 2 * 4 + sdm.sdm_footprint_bytes(0, 1, 0) - (1 * 20 + 2 * 4)
     big = sdm.sdm_footprint_bytes(2**20, 1, 2**20)
-    assert big > 2**20 * 20 + 2**20 * 16
+    assert big > 2**20 * 20 + 2**20 * 8  # state, then rank and perm per SD of a big cell
 
 
 def test_tuning_round_trip_and_validation(lib):
