@@ -191,6 +191,10 @@ struct sdm_ctx {
     int32_t *d_cell_off = nullptr;
     InstDev *d_inst = nullptr;
     std::vector<int32_t> h_cell_off;
+    // page-locked host staging of sdm_set_attributes' small transfers (the
+    // validation block in; offsets and the record out), kept between calls
+    unsigned char *h_pin = nullptr;
+    size_t h_pin_bytes = 0;
     int64_t device_bytes = 0;
     sdm_batch *self_batch = nullptr;
 };
@@ -923,16 +927,35 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     uint32_t *d_flags = d_counts + n_groups;
     unsigned long long *d_bad = (unsigned long long *)(((uintptr_t)(d_flags + 1) + 7) & ~(uintptr_t)7);
     // d_bad lies inside the 16 spare bytes after the counts
+    // page-locked staging: the validation block, then poff and uoff (n_groups
+    // + 1 each), then the run's record (64-byte aligned pieces)
+    auto a64 = [](size_t x) { return (x + 63) & ~(size_t)63; };
+    const size_t p_off = a64(b_counts), p_rec = p_off + a64(sizeof(int32_t) * 2 * (n_groups + 1));
+    const size_t b_pin = p_rec + a64(sizeof(InstDev));
+    if (ctx->h_pin_bytes < b_pin) {
+        if (ctx->h_pin)
+            cudaFreeHost(ctx->h_pin);
+        ctx->h_pin = nullptr;
+        ctx->h_pin_bytes = 0;
+        if (cudaHostAlloc((void **)&ctx->h_pin, b_pin, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_pin = nullptr;
+            mem.put(meta, b_counts);
+            mem.put(stage, b_stage);
+            return fail(&ctx->error, SDM_ENOMEM, "page-locked host staging allocation failed");
+        }
+        ctx->h_pin_bytes = b_pin;
+    }
     CTX_CUDA(ctx, cudaMemsetAsync(meta, 0, b_counts, s));
     CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
     validate_count_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_counts, d_flags, d_bad);
-    std::vector<uint32_t> counts(n_groups);
-    uint32_t flags = 0;
-    unsigned long long bad = 0;
-    CTX_CUDA(ctx, cudaMemcpyAsync(counts.data(), d_counts, sizeof(uint32_t) * n_groups, cudaMemcpyDeviceToHost, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(&flags, d_flags, sizeof flags, cudaMemcpyDeviceToHost, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+    // one copy of the whole block (counts, flags, first bad index)
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->h_pin, meta, b_counts, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    const uint32_t *counts = (const uint32_t *)ctx->h_pin;
+    const uint32_t flags = counts[n_groups];
+    const unsigned long long bad =
+        *(const unsigned long long *)(ctx->h_pin + ((uintptr_t)d_bad - (uintptr_t)meta));
     if (flags & 1u) {
         mem.put(meta, b_counts);
         mem.put(stage, b_stage);
@@ -941,7 +964,8 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     }
     // padded layout: every group starts at an even slot; the SDs outside the
     // domain follow the last cell
-    std::vector<int32_t> poff(n_groups + 1), uoff(n_groups + 1);
+    int32_t *poff = (int32_t *)(ctx->h_pin + p_off);
+    int32_t *uoff = poff + (n_groups + 1);
     int64_t ps = 0, us = 0;
     int32_t largest = 0;
     for (int32_t c = 0; c < n_groups; ++c) {
@@ -965,7 +989,7 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
             std::memcpy(hcell.data(), cell_id, b_c);
         }
         pos.resize(n_sd);
-        std::vector<int32_t> fill(poff.begin(), poff.end() - 1);
+        std::vector<int32_t> fill(poff, poff + n_groups);
         for (int64_t i = 0; i < n_sd; ++i)
             pos[i] = fill[hcell[i] < 0 ? n_cells : hcell[i]]++;
     }
@@ -979,31 +1003,30 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     int32_t *d_poff = (int32_t *)aux;
     int32_t *d_uoff = d_poff + (n_groups + 1);
     int32_t *d_pos = pos.empty() ? nullptr : d_uoff + (n_groups + 1);
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_poff, poff.data(), sizeof(int32_t) * (n_groups + 1), cudaMemcpyHostToDevice, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_uoff, uoff.data(), sizeof(int32_t) * (n_groups + 1), cudaMemcpyHostToDevice, s));
+    // poff and uoff lie back to back in both buffers: one copy
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_poff, poff, sizeof(int32_t) * 2 * (n_groups + 1), cudaMemcpyHostToDevice, s));
     if (d_pos)
         CTX_CUDA(ctx, cudaMemcpyAsync(d_pos, pos.data(), b_c, cudaMemcpyHostToDevice, s));
     // a context's own launch plan depends only on the padded layout and the
     // launch tuning: kept when both are unchanged
-    std::vector<int32_t> cell_off(poff.begin(), poff.begin() + n_cells + 1);
+    std::vector<int32_t> cell_off(poff, poff + n_cells + 1);
     const bool keep_plan = ctx->self_batch && ctx->h_cell_off == cell_off &&
                            same_tuning(ctx->self_batch->plan.tuning, current_tuning());
     ctx->n_sd = n_sd;
     ctx->n_slots = ps;
     ctx->largest_cell = largest;
-    ctx->h_cell_off = cell_off;
+    ctx->h_cell_off = std::move(cell_off);
     ctx->has_positions = false;
     ctx->layout_version += 1;
     ctx->dev_base = ctx->step;
-    InstDev inst = make_inst(ctx);
-    // Copies from pageable memory wait for the stream's earlier work, so the
-    // small ones (offsets, the record) go before the layout kernels; their
-    // sources are staged before the copies return, the caller's arrays were
-    // read before the validation sync, and the scratch is released in
-    // stream order: nothing waits for the kernels below.
-    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff.data(), sizeof(int32_t) * (n_cells + 1),
-                                  cudaMemcpyHostToDevice, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
+    InstDev *inst = (InstDev *)(ctx->h_pin + p_rec);
+    *inst = make_inst(ctx);
+    // The small copies come from the page-locked staging and return at
+    // once; the next call writes that staging only after its own
+    // synchronisation, which follows these copies on the stream.  The
+    // scratch is released in stream order: nothing waits for the kernels.
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_cell_off, poff, sizeof(int32_t) * (n_cells + 1), cudaMemcpyHostToDevice, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, inst, sizeof *inst, cudaMemcpyHostToDevice, s));
     fill_padding_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, d_poff, d_uoff, ctx->d_xi, ctx->d_v,
                                                                 ctx->d_id_of_slot);
     scatter_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_poff, d_uoff, d_pos, ctx->d_xi, ctx->d_v,
@@ -1173,6 +1196,8 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     sed_release(ctx);
     ctx->mem.release_kept();
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (ctx->h_pin)
+        cudaFreeHost(ctx->h_pin);
     delete ctx;
     if (e != cudaSuccess)
         return fail(nullptr, SDM_ECUDA, "sdm_destroy: %s", cudaGetErrorString(e));
