@@ -195,6 +195,9 @@ struct sdm_ctx {
     // validation block in; offsets and the record out), kept between calls
     unsigned char *h_pin = nullptr;
     size_t h_pin_bytes = 0;
+    // page-locked staging of sdm_spectrum (edges and dln in, the status word
+    // back), used when the result goes to the host (the call synchronises)
+    unsigned char *h_spec = nullptr;
     int64_t device_bytes = 0;
     sdm_batch *self_batch = nullptr;
 };
@@ -1104,6 +1107,17 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     const size_t b_edges = sizeof(double) * host_e.size(), b_acc = sizeof(double) * n_out;
     const size_t b_part = total ? sizeof(double) * (size_t)grid * nb : b_acc;
     const size_t b_tmp = b_edges + b_part + b_acc;
+    // host result: the edges go out of, and the status word comes back into,
+    // page-locked staging (the call synchronises before it returns, so the
+    // next call finds the staging free)
+    constexpr size_t kSpecPin = sizeof(double) * 2 * kMaxEdges + 64;
+    if (!out_on_device && !ctx->h_spec) {
+        if (cudaHostAlloc((void **)&ctx->h_spec, kSpecPin, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->h_spec = nullptr;
+            return fail(&ctx->error, SDM_ENOMEM, "page-locked host staging allocation failed");
+        }
+    }
     char *tmp = (char *)ctx->mem.get(b_tmp);
     if (!tmp)
         return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
@@ -1111,7 +1125,12 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     const double *d_dln = d_edges + n_edges;
     double *d_acc = (double *)(tmp + b_edges);
     double *d_out = out_on_device ? out : (double *)(tmp + b_edges + b_part);
-    CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, host_e.data(), b_edges, cudaMemcpyHostToDevice, s));
+    const double *src_e = host_e.data();
+    if (!out_on_device) {
+        std::memcpy(ctx->h_spec, host_e.data(), b_edges);
+        src_e = (const double *)ctx->h_spec;
+    }
+    CTX_CUDA(ctx, cudaMemcpyAsync(d_edges, src_e, b_edges, cudaMemcpyHostToDevice, s));
     const double vol = per_cell ? ctx->cfg.dv : ctx->cfg.dv * (double)ctx->cfg.n_cells;
     if (total) {
         spectrum_total_kernel<<<grid, kSpecTotNT, 0, s>>>(ctx->d_inst, ctx->h_cell_off[ctx->cfg.n_cells], d_edges,
@@ -1124,10 +1143,14 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     }
     CTX_CUDA(ctx, cudaGetLastError());
     if (!out_on_device) {
+        uint32_t *h_status = (uint32_t *)(ctx->h_spec + sizeof(double) * 2 * kMaxEdges);
         CTX_CUDA(ctx, cudaMemcpyAsync(out, d_out, b_acc, cudaMemcpyDeviceToHost, s));
+        CTX_CUDA(ctx, cudaMemcpyAsync(h_status, &ctx->d_inst->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
         CTX_CUDA(ctx, cudaStreamSynchronize(s));
         ctx->mem.put(tmp, b_tmp);
-        return check_device_status(ctx);
+        if (*h_status & 1u)
+            return fail(&ctx->error, SDM_ETIMEOUT, "a device-side wait for a bulk copy gave up; results are incomplete");
+        return SDM_OK;
     }
     ctx->mem.put(tmp, b_tmp);
     return SDM_OK;
@@ -1198,6 +1221,8 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (ctx->h_pin)
         cudaFreeHost(ctx->h_pin);
+    if (ctx->h_spec)
+        cudaFreeHost(ctx->h_spec);
     delete ctx;
     if (e != cudaSuccess)
         return fail(nullptr, SDM_ECUDA, "sdm_destroy: %s", cudaGetErrorString(e));
