@@ -1616,16 +1616,17 @@ __global__ void spectrum_finalize_kernel(const double *__restrict__ acc, const d
 // invalid attribute (first bad SD index in *bad); bit 1: groups not sorted.
 // Each warp takes 32 consecutive SDs at a time and adds one count per run of
 // equal groups (one or two atomics per warp for sorted input).
-__global__ void validate_count_kernel(int64_t n_sd, const int64_t *__restrict__ xi, const double *__restrict__ v,
-                                      const int32_t *__restrict__ cell, int32_t n_cells, uint32_t *__restrict__ counts,
-                                      uint32_t *__restrict__ flags, unsigned long long *__restrict__ bad)
+__global__ void validate_count_kernel(int64_t lo, int64_t hi, const int64_t *__restrict__ xi,
+                                      const double *__restrict__ v, const int32_t *__restrict__ cell, int32_t n_cells,
+                                      uint32_t *__restrict__ counts, uint32_t *__restrict__ flags,
+                                      unsigned long long *__restrict__ bad)
 {
     constexpr unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_sd; base += wstride) {
+    for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < hi; base += wstride) {
         const int64_t i = base + lane;
-        const bool in = i < n_sd;
+        const bool in = i < hi;
         const int32_t c_in = in ? cell[i] : INT32_MAX;
         const int32_t craw = c_in == -1 ? n_cells : c_in; // the group; outside sorts last
         int32_t c = -1;                                     // counted group, -1: none

@@ -133,6 +133,8 @@ struct Buf {
     size_t bytes = 0;
 };
 
+constexpr int kInChunks = 4; // pieces of a host input copy (sdm_set_attributes)
+
 // Cell-size classes of the shared-memory path.
 constexpr int kClassCap[] = {64, 128, 256, 512, 1024, 2048, 4096};
 constexpr int kNumClass = sizeof(kClassCap) / sizeof(kClassCap[0]);
@@ -198,6 +200,10 @@ struct sdm_ctx {
     // page-locked staging of sdm_spectrum (edges and dln in, the status word
     // back), used when the result goes to the host (the call synchronises)
     unsigned char *h_spec = nullptr;
+    // copies of host input run on their own stream, in kInChunks pieces, so
+    // that each piece is validated while the next one is on its way
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t in_ev[kInChunks + 1] = {};
     int64_t device_bytes = 0;
     sdm_batch *self_batch = nullptr;
 };
@@ -905,17 +911,40 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     const double *dv = volume;
     const int32_t *dcell = cell_id;
     const size_t b_stage = b_xi + b_v + b_c;
+    // SD ranges of the pieces (one piece for device input)
+    const int n_in = on_device ? 1 : kInChunks;
+    int64_t piece[kInChunks + 1];
+    for (int k = 0; k <= n_in; ++k)
+        piece[k] = n_sd * k / n_in;
     if (!on_device) {
         stage = mem.get(b_stage);
         if (!stage)
             return fail(&ctx->error, SDM_ENOMEM, "staging allocation failed");
+        if (!ctx->cstream) {
+            CTX_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+            for (cudaEvent_t &ev : ctx->in_ev)
+                CTX_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        }
         char *p = (char *)stage;
-        CTX_CUDA(ctx, cudaMemcpyAsync(p, xi, b_xi, cudaMemcpyHostToDevice, s));
-        CTX_CUDA(ctx, cudaMemcpyAsync(p + b_xi, volume, b_v, cudaMemcpyHostToDevice, s));
-        CTX_CUDA(ctx, cudaMemcpyAsync(p + b_xi + b_v, cell_id, b_c, cudaMemcpyHostToDevice, s));
         dxi = (const int64_t *)p;
         dv = (const double *)(p + b_xi);
         dcell = (const int32_t *)(p + b_xi + b_v);
+        // the copy stream starts after the stream's earlier work (the staging
+        // block is free in that order); piece k's copies, then its event
+        CTX_CUDA(ctx, cudaEventRecord(ctx->in_ev[kInChunks], s));
+        CTX_CUDA(ctx, cudaStreamWaitEvent(ctx->cstream, ctx->in_ev[kInChunks], 0));
+        for (int k = 0; k < n_in; ++k) {
+            const int64_t a = piece[k], n = piece[k + 1] - piece[k];
+            if (n > 0) {
+                CTX_CUDA(ctx, cudaMemcpyAsync((void *)(dxi + a), xi + a, sizeof(int64_t) * n, cudaMemcpyHostToDevice,
+                                              ctx->cstream));
+                CTX_CUDA(ctx, cudaMemcpyAsync((void *)(dv + a), volume + a, sizeof(double) * n,
+                                              cudaMemcpyHostToDevice, ctx->cstream));
+                CTX_CUDA(ctx, cudaMemcpyAsync((void *)(dcell + a), cell_id + a, sizeof(int32_t) * n,
+                                              cudaMemcpyHostToDevice, ctx->cstream));
+            }
+            CTX_CUDA(ctx, cudaEventRecord(ctx->in_ev[k], ctx->cstream));
+        }
     }
     // counts per group (the cells, then the SDs outside the domain), flags,
     // first bad index
@@ -951,7 +980,13 @@ sdm_status sdm_set_attributes(sdm_ctx *ctx, int64_t n_sd, const int64_t *xi, con
     }
     CTX_CUDA(ctx, cudaMemsetAsync(meta, 0, b_counts, s));
     CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
-    validate_count_kernel<<<1216, 256, 0, s>>>(n_sd, dxi, dv, dcell, n_cells, d_counts, d_flags, d_bad);
+    for (int k = 0; k < n_in; ++k) { // piece k once it has landed (pieces land in order)
+        if (!on_device)
+            CTX_CUDA(ctx, cudaStreamWaitEvent(s, ctx->in_ev[k], 0));
+        if (piece[k + 1] > piece[k])
+            validate_count_kernel<<<1216, 256, 0, s>>>(piece[k], piece[k + 1], dxi, dv, dcell, n_cells, d_counts,
+                                                        d_flags, d_bad);
+    }
     // one copy of the whole block (counts, flags, first bad index)
     CTX_CUDA(ctx, cudaMemcpyAsync(ctx->h_pin, meta, b_counts, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
@@ -1223,6 +1258,13 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
         cudaFreeHost(ctx->h_pin);
     if (ctx->h_spec)
         cudaFreeHost(ctx->h_spec);
+    for (cudaEvent_t ev : ctx->in_ev)
+        if (ev)
+            cudaEventDestroy(ev);
+    if (ctx->cstream) {
+        cudaStreamSynchronize(ctx->cstream);
+        cudaStreamDestroy(ctx->cstream);
+    }
     delete ctx;
     if (e != cudaSuccess)
         return fail(nullptr, SDM_ECUDA, "sdm_destroy: %s", cudaGetErrorString(e));
