@@ -229,25 +229,55 @@ def test_big_cell_path(env):
     run.close()
 
 
-def test_large_single_cell_full_size(env):
-    """2^20 SDs in one cell (the single-large-cell workload), 2 steps."""
+@pytest.mark.parametrize("seed", [0, 1])
+def test_large_single_cell_full_size(env, seed):
+    """2^20 SDs in one cell (the single-large-cell workload, two of its
+    ensemble seeds), 12 steps through the multi-pass path, batched as the
+    benchmark steps it."""
     O, sdm, torch = env
-    g = I.box_golovin(2**20, seed=31)
-    run = _gpu_run(sdm, "golovin", "fp64", g.xi, g.v, g.cell, 1, g.dv, 31, 2)
+    g = I.box_golovin(2**20, seed=seed)
+    run = sdm.Run(sdm.make_config("golovin", "fp64", dv=g.dv, seed=seed), g.n_sd).set_attributes(g.xi, g.v, g.cell)
+    batch = sdm.Batch([run])
+    batch.step(5)
+    batch.step(7)
+    torch.cuda.synchronize()
+    batch.close()
     gx, gv = run.attributes()
-    st = _oracle_run(O, "golovin", "fp64", g.xi, g.v, g.cell, 1, g.dv, 31, 2)
-    _assert_same(gx, gv, st, "2^20 cell")
+    st = _oracle_run(O, "golovin", "fp64", g.xi, g.v, g.cell, 1, g.dv, seed, 12)
+    _assert_same(gx, gv, st, f"2^20 cell seed {seed}")
+    assert int((gx != g.xi).sum()) > 0
     run.close()
 
 
-def test_full_grid_two_steps(env):
+def test_ensemble_members_match_the_oracle(env):
+    """Every 8th member of the 1024-box ensemble (n_sd = 2^U(8,16): warp,
+    block and multi-pass cells side by side), 20 steps as one batch replayed
+    from a CUDA graph, each member against the oracle run alone."""
+    O, sdm, torch = env
+    insts = I.batched_ensemble(steps=20)[::8]
+    runs = [sdm.Run(sdm.make_config("golovin", "fp64", dv=t.dv, seed=t.seed), t.n_sd).set_attributes(t.xi, t.v, t.cell)
+            for t in insts]
+    assert min(t.n_sd for t in insts) < 512 and max(t.n_sd for t in insts) > 4096
+    batch = sdm.Batch(runs, use_graph=True, graph_steps=5)
+    batch.step(20)
+    torch.cuda.synchronize()
+    batch.close()
+    for t, r in zip(insts, runs):
+        gx, gv = r.attributes()
+        st = _oracle_run(O, "golovin", "fp64", t.xi, t.v, t.cell, 1, t.dv, t.seed, 20)
+        _assert_same(gx, gv, st, f"ensemble member n_sd={t.n_sd} seed={t.seed}")
+        r.close()
+
+
+def test_full_grid(env):
     """The 128 x 128 x 256 geometric grid (4.19M SDs) in the launch
-    configuration the benchmark times, 2 steps, every SD compared."""
+    configuration the benchmark times (one step per call), 12 steps, every
+    SD compared."""
     O, sdm, torch = env
     g = I.grid_geometric(seed=0)
-    run = _gpu_run(sdm, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 2, chunks=[1, 1])
+    run = _gpu_run(sdm, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 12, chunks=[1] * 12)
     gx, gv = run.attributes()
-    st = _oracle_run(O, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 2)
+    st = _oracle_run(O, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 12)
     _assert_same(gx, gv, st, "full grid")
     got = run.spectrum(I.R_EDGES)
     want = O.spectrum(O.params("geometric", dv=g.dv), st, I.R_EDGES)
