@@ -52,7 +52,7 @@ WORKLOAD = ("grid_geometric: 128x128 cells x 256 SDs (4,194,304 SDs), dV=1e3 m^3
 KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
-EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "serving", "sedimentation")
+EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "fused", "serving", "sedimentation")
 
 
 # The step kernel and every helper it uses: the device header, and the kernel
@@ -279,6 +279,8 @@ def run_ours(args, rank: int, world: int):
             extras["large_cells"] = measure_large_cells(sdm, torch)
         if "kfp32" in wanted:
             extras["kfp32"] = measure_kfp32(sdm, torch, g)
+        if "fused" in wanted:
+            extras["fused"] = measure_fused(sdm, torch, g)
         if "serving" in wanted:
             extras["serving"] = measure_serving(torch, args.serve_requests)
         if "sedimentation" in wanted:
@@ -493,6 +495,33 @@ def measure_kfp32(sdm, torch, g, steps=600):
     out["spectrum_rel_l1_kfp32_vs_fp64"] = float(np.abs(b - a).sum() / np.abs(a).sum())
     out["steps"] = steps
     out["note"] = "state resident, no L2 flush between steps (state 67 MB)"
+    return out
+
+
+def measure_fused(sdm, torch, g, steps=600):
+    """The grid's whole 600-step run in one call: one launch per step against
+    fused launches that keep every cell in shared memory for 8, 32 or 600
+    steps.  The final states must be identical."""
+    pairs = pairs_per_step(g.xi, g.cell, g.n_cells)
+    out = {"steps": steps, "note": "one sdm_coalescence_step call of 600 steps; state resident, no L2 flush"}
+    ref = None
+    try:
+        for f in (0, 8, 32, 600):
+            sdm.sdm_set_tuning({"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": f})
+            run = sdm.Run(sdm.make_config("geometric", "fp64", dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+            run.set_attributes(g.xi, g.v, g.cell).step(0)
+            dt = _timed(torch, lambda: run.step(steps))
+            xi, v = run.attributes()
+            run.close()
+            key = "per_step_launch" if f == 0 else f"fuse_{f}"
+            out[key + "_pair_updates_per_s"] = pairs * steps / dt
+            out[key + "_ms_per_step"] = dt * 1e3 / steps
+            if ref is None:
+                ref = (xi, v)
+            else:
+                out[key + "_state_identical"] = bool(np.array_equal(xi, ref[0]) and np.array_equal(v, ref[1]))
+    finally:
+        sdm.sdm_set_tuning(None)
     return out
 
 

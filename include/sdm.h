@@ -248,7 +248,12 @@ typedef struct sdm_tuning {
     int32_t smem_max_sd;     /* largest cell sorted in shared memory: 512, 1024, 2048 or 4096 (default) */
     int32_t warp_cell_max;   /* largest cell run by one warp: 0, 64, 128, 256 or 512 (default), <= smem_max_sd */
     int32_t warps_per_block; /* warps per block of the warp-per-cell kernel: 1, 2 (default) or 4 */
-    int32_t reserved0;       /* must be 0 */
+    int32_t fuse_steps;      /* 0 or 1 (default): one launch per step.  2..1024: the warp-per-cell
+                              * kernel keeps each cell in shared memory for up to fuse_steps
+                              * consecutive steps of one sdm_batch_step / sdm_coalescence_step call
+                              * (the same state, bit for bit: cells are independent, so a cell may
+                              * take its steps apart from the others); cells of other sizes still
+                              * take one launch per step.  A graph captures the same launches. */
 } sdm_tuning;
 
 /* NULL restores the defaults.  Errors: SDM_EINVAL. */

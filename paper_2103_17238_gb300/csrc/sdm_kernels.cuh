@@ -556,10 +556,14 @@ __device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cel
     return c;
 }
 
-template <int CAP, int WARPS, int STAGES>
+// FUSED: every cell stays in its stage for n_fused consecutive steps (its
+// updates go to the stage, which returns to global memory at the end), for
+// runs whose steps have no other dynamic in between; cells are independent,
+// so this is the same sequence of steps per cell.  Otherwise one step.
+template <int CAP, int WARPS, int STAGES, bool FUSED = false>
 __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
                                                                     InstDev *const *__restrict__ insts,
-                                                                    int64_t step_offset)
+                                                                    int64_t step_offset, int32_t n_fused = 1)
 {
     constexpr int NB = CAP;
     constexpr int LB = ilog2_c(CAP);
@@ -669,12 +673,31 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
         const int n = meta.y;
         const uint32_t cell = (uint32_t)meta.z;
         InstDev *__restrict__ P = insts[meta.w];
-        const int64_t s = P->step + step_offset;
+        const int64_t s0 = P->step + step_offset;
         const uint64_t seed = P->seed;
-        const int64_t *xs = st_xi + sg * CAP;
-        const double *vs = st_v + sg * CAP;
+        int64_t *xs = st_xi + sg * CAP;
+        double *vs = st_v + sg * CAP;
         int64_t *__restrict__ gxi = P->xi + meta.x;
         double *__restrict__ gv = P->v + meta.x;
+        // a changed pair goes to global memory, or in FUSED mode to the stage
+        auto put_pair = [&](uint32_t a, uint32_t b, int64_t xa, int64_t xb, double va, double vb, bool split) {
+            if constexpr (FUSED) {
+                xs[a] = xa;
+                xs[b] = xb;
+                vs[b] = vb;
+                if (split)
+                    vs[a] = va;
+            } else {
+                gxi[a] = xa;
+                gxi[b] = xb;
+                gv[b] = vb;
+                if (split)
+                    gv[a] = va;
+            }
+        };
+        const int n_rep = FUSED ? n_fused : 1;
+        for (int rep = 0; rep < n_rep; ++rep) { // warp-uniform
+        const int64_t s = s0 + rep;
 
 #pragma unroll
         for (int i = 0; i < BPL; ++i)
@@ -910,14 +933,24 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                     int64_t xa = xs[a], xb = xs[b];
                     double va = vs[a], vb = vs[b];
                     const bool split = shima_update(cap_gamma(gf, xa, xb), xa, xb, va, vb);
-                    gxi[a] = xa;
-                    gxi[b] = xb;
-                    gv[b] = vb;
-                    if (split)
-                        gv[a] = va;
+                    put_pair(a, b, xa, xb, va, vb, split);
                 }
-                // pairs the filter could not decide wait for the exact evaluation
+                // pairs the filter could not decide: in FUSED mode evaluated
+                // exactly at once (from the stage); otherwise they wait in the
+                // queue for the exact evaluation
                 const bool und = gf < 0;
+                if constexpr (FUSED) {
+                    if (und) {
+                        int64_t xa = xs[a], xb = xs[b];
+                        double va = vs[a], vb = vs[b];
+                        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                        if (g > 0) {
+                            const bool split = shima_update(g, xa, xb, va, vb);
+                            put_pair(a, b, xa, xb, va, vb, split);
+                        }
+                    }
+                    continue;
+                }
                 const unsigned m = __ballot_sync(FULL, und);
                 if (m) {
                     const uint32_t base = s_qn;
@@ -939,11 +972,7 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                             const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
                             if (g > 0) {
                                 const bool split = shima_update(g, xa, xb, va, vb);
-                                gxi[a] = xa;
-                                gxi[b] = xb;
-                                gv[b] = vb;
-                                if (split)
-                                    gv[a] = va;
+                                put_pair(a, b, xa, xb, va, vb, split);
                             }
                         }
                     }
@@ -954,7 +983,19 @@ __global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkIt
                 }
             }
         }
-        __syncwarp(); // stage sg and the work arrays are free again
+        __syncwarp(); // the work arrays are free again
+        } // rep
+        if constexpr (FUSED) { // the cell back to global memory
+            for (int i = lane; i < n; i += 32) {
+                gxi[i] = xs[i];
+                gv[i] = vs[i];
+            }
+            // the stage was written through the generic proxy; the next bulk
+            // copy into it goes through the async proxy
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+        }
+        // stage sg is free again
         if (s_qn >= 32u)
             flush();
     }

@@ -313,11 +313,22 @@ void launch_warp(int grid, int n, const WorkItem *items, InstDev *const *insts, 
                                                                                                      off);
 }
 
+// The fused form (every cell stays in shared memory for nf steps) always runs
+// 2 warps per block.
+template <int CAP>
+void launch_warp_fused(int grid, int n, const WorkItem *items, InstDev *const *insts, int64_t off, int32_t nf,
+                       cudaStream_t st)
+{
+    warp_cell_step_kernel<CAP, 2, 2, true><<<grid, 64, WarpSmem<CAP, 2>::per_warp * 2, st>>>(items, n, insts, off, nf);
+}
+
 template <int CAP, int NT, int ST>
 void launch_block(int grid, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
 {
     cell_step_kernel<CAP, NT, ST><<<grid, NT, CellSmem<CAP, ST>::bytes, st>>>(items, n, insts, off);
 }
+
+typedef void (*fused_fn)(int grid, int n, const WorkItem *, InstDev *const *, int64_t, int32_t, cudaStream_t);
 
 struct Variant {
     int cap;
@@ -325,6 +336,17 @@ struct Variant {
     launch_fn launch;
     int max_grid; // resident blocks x SMs (set at configuration)
 };
+
+// the fused warp kernels by capacity 64 .. 512
+struct FusedVariant {
+    int cap;
+    fused_fn launch;
+    int max_grid;
+};
+FusedVariant g_fused[] = {{64, launch_warp_fused<64>, 0},
+                          {128, launch_warp_fused<128>, 0},
+                          {256, launch_warp_fused<256>, 0},
+                          {512, launch_warp_fused<512>, 0}};
 
 Variant g_variants[] = {
 #define X(CAP, WARPS) {CAP, WARPS, launch_warp<CAP, WARPS>, 0},
@@ -344,7 +366,7 @@ sdm_tuning g_tuning = {4096, 512, 2, 0};
 bool same_tuning(const sdm_tuning &a, const sdm_tuning &b)
 {
     return a.smem_max_sd == b.smem_max_sd && a.warp_cell_max == b.warp_cell_max &&
-           a.warps_per_block == b.warps_per_block;
+           a.warps_per_block == b.warps_per_block && a.fuse_steps == b.fuse_steps;
 }
 
 sdm_tuning current_tuning()
@@ -402,6 +424,21 @@ cudaError_t configure_kernels_once()
         g_variants[v++].max_grid = std::max(1, per_sm) * sms;                                                          \
     }
         SDM_BLOCK_VARIANTS(X)
+#undef X
+        v = 0;
+#define X(CAP)                                                                                                         \
+    {                                                                                                                  \
+        const int bytes = (int)(WarpSmem<CAP, 2>::per_warp * 2);                                                       \
+        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, 2, 2, true>,                                          \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)             \
+            e = r;                                                                                                     \
+        int per_sm = 0;                                                                                                \
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, 2, 2, true>, 64,    \
+                                                               bytes)) != cudaSuccess)                                 \
+            e = r;                                                                                                     \
+        g_fused[v++].max_grid = std::max(1, per_sm) * sms;                                                             \
+    }
+        X(64) X(128) X(256) X(512)
 #undef X
         int spec_per_sm = 0;
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spec_per_sm, spectrum_total_kernel, kSpecTotNT, 0)) !=
@@ -558,12 +595,10 @@ sdm_status build_plan(sdm_batch *b)
     return SDM_OK;
 }
 
-// Enqueues one step (offset `off` from each run's device counter) of every cell.
-void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
+// One step (offset `off` from each run's device counter) of every cell above
+// the shared-memory threshold.
+void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
 {
-    for (int k = 0; k < kNumClass; ++k)
-        if (pl.n_items[k])
-            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
     if (pl.n_big) {
         const size_t hs = big_hist_smem(pl.max_big_lb);
         big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
@@ -577,11 +612,51 @@ void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
     }
 }
 
+// Enqueues one step (offset `off` from each run's device counter) of every cell.
+void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
+{
+    for (int k = 0; k < kNumClass; ++k)
+        if (pl.n_items[k])
+            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
+    enqueue_big(pl, off, st);
+}
+
+// Enqueues n steps (offsets off .. off + n - 1) of every cell.  Cells are
+// independent, so each one may take its n steps apart from the others: with
+// fusion on (tuning fuse_steps f >= 2) the warp-per-cell classes take up to f
+// steps per launch, the other cells one launch per step.
+void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
+{
+    const int32_t f = pl.tuning.fuse_steps;
+    if (f < 2 || n < 2) {
+        for (int32_t i = 0; i < n; ++i)
+            enqueue_step(pl, off + i, st);
+        return;
+    }
+    for (int32_t i = 0; i < n; i += f) {
+        const int32_t m = std::min(f, n - i);
+        for (int k = 0; k < kNumClass; ++k) {
+            if (!pl.n_items[k])
+                continue;
+            const Variant &x = g_variants[pl.variant[k]];
+            if (x.warps > 0) {
+                const FusedVariant &fv = g_fused[k];
+                const int grid = std::min((pl.n_items[k] + 1) / 2, fv.max_grid);
+                fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, m, st);
+            } else {
+                for (int32_t j = 0; j < m; ++j)
+                    launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i + j, st);
+            }
+        }
+        for (int32_t j = 0; j < m; ++j)
+            enqueue_big(pl, off + i + j, st);
+    }
+}
+
 // A captured graph: n steps from the device counters, then the counters advance by n.
 void enqueue_graph_body(const Plan &pl, int32_t n, cudaStream_t st)
 {
-    for (int32_t i = 0; i < n; ++i)
-        enqueue_step(pl, i, st);
+    enqueue_steps(pl, 0, n, st);
     advance_steps_kernel<<<(pl.n_inst + 255) / 256, 256, 0, st>>>(pl.d_insts, pl.n_inst, n, nullptr);
 }
 
@@ -706,8 +781,7 @@ sdm_status batch_step(sdm_batch *b, int32_t n_steps)
         }
     }
     const int64_t off0 = b->ctxs[0]->step - b->ctxs[0]->dev_base;
-    for (int32_t i = 0; i < left; ++i)
-        enqueue_step(b->plan, off0 + i, b->stream);
+    enqueue_steps(b->plan, off0, left, b->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return cuda_fail(b, e, "step launch");
@@ -1328,10 +1402,11 @@ sdm_status sdm_set_tuning(const sdm_tuning *t)
         const bool warp_ok = t->warp_cell_max == 0 || t->warp_cell_max == 64 || t->warp_cell_max == 128 ||
                              t->warp_cell_max == 256 || t->warp_cell_max == 512;
         const bool wpb_ok = t->warps_per_block == 1 || t->warps_per_block == 2 || t->warps_per_block == 4;
-        if (!smem_ok || !warp_ok || !wpb_ok || t->reserved0 != 0 || t->warp_cell_max > t->smem_max_sd)
+        const bool fuse_ok = t->fuse_steps >= 0 && t->fuse_steps <= 1024;
+        if (!smem_ok || !warp_ok || !wpb_ok || !fuse_ok || t->warp_cell_max > t->smem_max_sd)
             return fail(nullptr, SDM_EINVAL,
                         "tuning: smem_max_sd in {512,1024,2048,4096}, warp_cell_max in {0,64,128,256,512} and <= "
-                        "smem_max_sd, warps_per_block in {1,2,4}, reserved0 = 0");
+                        "smem_max_sd, warps_per_block in {1,2,4}, fuse_steps in 0..1024");
         v = *t;
     }
     std::lock_guard<std::mutex> lock(g_tuning_mutex);

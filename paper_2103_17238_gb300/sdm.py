@@ -73,7 +73,7 @@ class sdm_tuning(ctypes.Structure):
         ("smem_max_sd", ctypes.c_int32),
         ("warp_cell_max", ctypes.c_int32),
         ("warps_per_block", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("fuse_steps", ctypes.c_int32),
     ]
 
 
@@ -361,18 +361,21 @@ def sdm_get_positions(ctx, n_sd: int | None = None, z=None, cell=None, want_z: b
 
 
 def sdm_set_tuning(tuning=None):
-    """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block; None: defaults."""
+    """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block and
+    optionally fuse_steps (default 0: one launch per step); None: defaults."""
     if tuning is None:
         _check(load().sdm_set_tuning(None), "sdm_set_tuning")
         return
-    t = sdm_tuning(int(tuning["smem_max_sd"]), int(tuning["warp_cell_max"]), int(tuning["warps_per_block"]), 0)
+    t = sdm_tuning(int(tuning["smem_max_sd"]), int(tuning["warp_cell_max"]), int(tuning["warps_per_block"]),
+                   int(tuning.get("fuse_steps", 0)))
     _check(load().sdm_set_tuning(ctypes.byref(t)), "sdm_set_tuning")
 
 
 def sdm_get_tuning() -> dict:
     t = sdm_tuning()
     _check(load().sdm_get_tuning(ctypes.byref(t)), "sdm_get_tuning")
-    return {"smem_max_sd": t.smem_max_sd, "warp_cell_max": t.warp_cell_max, "warps_per_block": t.warps_per_block}
+    return {"smem_max_sd": t.smem_max_sd, "warp_cell_max": t.warp_cell_max, "warps_per_block": t.warps_per_block,
+            "fuse_steps": t.fuse_steps}
 
 
 # ------------------------------------------------------------ owners

@@ -96,10 +96,13 @@ def test_tuning_round_trip_and_validation(lib):
     range (the previous setting stays), restored by NULL."""
     from paper_2103_17238_gb300 import sdm
 
-    default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2}
+    default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": 0}
     sdm.sdm_set_tuning(None)
     assert sdm.sdm_get_tuning() == default
-    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4}
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 0}
+    sdm.sdm_set_tuning({k: t[k] for k in ("smem_max_sd", "warp_cell_max", "warps_per_block")})
+    assert sdm.sdm_get_tuning() == t
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 1024}
     sdm.sdm_set_tuning(t)
     assert sdm.sdm_get_tuning() == t
     for bad in ({"smem_max_sd": 8192, "warp_cell_max": 256, "warps_per_block": 2},
@@ -108,12 +111,14 @@ def test_tuning_round_trip_and_validation(lib):
                 {"smem_max_sd": 512, "warp_cell_max": 1024, "warps_per_block": 2},
                 {"smem_max_sd": 4096, "warp_cell_max": 96, "warps_per_block": 2},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 3},
-                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 0}):
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 0},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "fuse_steps": 1025},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "fuse_steps": -1}):
         with pytest.raises(sdm.SdmError) as e:
             sdm.sdm_set_tuning(bad)
         assert e.value.status == sdm.SDM_EINVAL
         assert sdm.sdm_get_tuning() == t
-    raw = sdm.sdm_tuning(4096, 256, 2, 1)  # reserved field must be zero
+    raw = sdm.sdm_tuning(4096, 256, 2, 2000)  # beyond the fusion limit
     assert lib.sdm_set_tuning(ctypes.byref(raw)) == sdm.SDM_EINVAL
     assert lib.sdm_get_tuning(None) == sdm.SDM_EINVAL
     # cells above the shared-memory threshold need multi-pass scratch

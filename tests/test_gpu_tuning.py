@@ -92,7 +92,7 @@ def test_autotuned_batch_equals_default(env, tmp_path):
     probe = make()
     rep = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert not rep["cached"] and rep["best"] in cands
-    assert sdm.sdm_get_tuning() == rep["best"]
+    assert sdm.sdm_get_tuning() == {"fuse_steps": 0, **rep["best"]}
     assert rep["ms_per_step"] <= rep["worst_ms_per_step"]
     again = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert again["cached"] and again["best"] == rep["best"]
@@ -108,3 +108,54 @@ def test_autotuned_batch_equals_default(env, tmp_path):
         x2, v2 = a.attributes()
         assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
     sdm.sdm_set_tuning(None)
+
+
+@pytest.mark.parametrize("kernel,precision,fuse", [("geometric", "fp64", 7), ("golovin", "kfp32", 2),
+                                                   ("geometric", "fp64", 1024)])
+def test_fused_steps_give_the_oracle_state(env, kernel, precision, fuse):
+    """With fusion on, every warp-per-cell cell takes up to `fuse` steps in one
+    launch, the other cells one launch per step; 10 steps split as 7 + 3, 5 x 2
+    and 1 x 10 must all end in the oracle's state, directly and in a graph."""
+    O, sdm, torch = env
+    xi, v, cell = _state(29)
+    nc, dv, seed, steps = len(SIZES), 1e3, 37, 10
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, nc)
+    O.run(O.params(kernel, precision, dv=dv, seed=seed), st, 0, steps)
+    sdm.sdm_set_tuning({"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": fuse})
+    try:
+        run = sdm.Run(sdm.make_config(kernel, precision, dv=dv, n_cells=nc, seed=seed), len(xi))
+        run.set_attributes(xi, v, cell).step(steps)
+        gx, gv = run.attributes()
+        run.close()
+        assert np.array_equal(gx, st.xi) and np.array_equal(gv, st.v)
+
+        runs = [sdm.Run(sdm.make_config(kernel, precision, dv=dv, n_cells=nc, seed=seed), len(xi))
+                .set_attributes(xi, v, cell) for _ in range(2)]
+        b = sdm.Batch(runs, use_graph=True, graph_steps=4)
+        b.step(steps)  # two graph launches of 4 steps, then 2 direct steps
+        torch.cuda.synchronize()
+        b.close()
+        for r in runs:
+            gx, gv = r.attributes()
+            r.close()
+            assert np.array_equal(gx, st.xi) and np.array_equal(gv, st.v)
+    finally:
+        sdm.sdm_set_tuning(None)
+
+
+def test_fused_grid_matches_the_oracle(env):
+    """A 24 x 24 grid of 256-SD cells (the shape of the flagship workload),
+    30 steps in fused launches of 16 + 14."""
+    O, sdm, torch = env
+    g = I.grid_geometric(side=24, sd_per_cell=256, seed=5)
+    st = O.State(g.xi.copy(), g.v.copy(), g.cell.copy(), None, g.n_cells)
+    O.run(O.params("geometric", "fp64", dv=g.dv, seed=g.seed), st, 0, 30)
+    sdm.sdm_set_tuning({"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": 16})
+    try:
+        run = sdm.Run(sdm.make_config("geometric", dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+        run.set_attributes(g.xi, g.v, g.cell).step(30)
+        gx, gv = run.attributes()
+        run.close()
+    finally:
+        sdm.sdm_set_tuning(None)
+    assert np.array_equal(gx, st.xi) and np.array_equal(gv, st.v)
