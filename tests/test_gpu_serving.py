@@ -30,13 +30,18 @@ def _stream(n=14):
     return reqs
 
 
-def test_served_equals_alone(env):
+@pytest.mark.parametrize("fuse", [0, 8])
+def test_served_equals_alone(env, fuse):
+    """Also with each tick's steps fused for the small cells; the tuning is
+    restored after every batch is built."""
     sdm, serve, torch = env
     reqs = _stream()
     fps = [serve.footprint(r.inst) for r in reqs]
     budget = 3 * max(fps)  # forces queueing: only a few runs fit at once
-    srv = serve.Server(budget, chunk=8, keep_state=True, time_scale=1.0)
+    srv = serve.Server(budget, chunk=8, keep_state=True, time_scale=1.0, fuse_steps=fuse)
+    before = sdm.sdm_get_tuning()
     out = srv.serve(reqs)
+    assert sdm.sdm_get_tuning() == before
     assert out["requests"] == len(reqs)
     assert out["step_latency_ms"]["p99"] is not None
     # admission respected the budget, and runs overlapped on the device
