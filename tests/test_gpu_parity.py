@@ -283,6 +283,16 @@ def test_full_grid(env):
     want = O.spectrum(O.params("geometric", dv=g.dv), st, I.R_EDGES)
     assert np.allclose(got, want, rtol=max(1e-12, 2 * g.n_sd * U), atol=0)
     run.close()
+    # the same 12 steps in fused launches (12, then 5 + 5 + 2), every SD compared
+    for fuse, chunks in ((12, [12]), (5, [12])):
+        sdm.sdm_set_tuning({"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": fuse})
+        try:
+            run = _gpu_run(sdm, "geometric", "fp64", g.xi, g.v, g.cell, g.n_cells, g.dv, 0, 12, chunks=chunks)
+        finally:
+            sdm.sdm_set_tuning(None)
+        gx, gv = run.attributes()
+        run.close()
+        _assert_same(gx, gv, st, f"full grid, fused by {fuse}")
 
 
 def test_sort_keys_sharing_their_top_bits(env):
