@@ -4,8 +4,8 @@
  * cpu_baseline / reference legs of bench.py may load or call this code.  The
  * product path (the CUDA library) never does, and the two share no source.
  *
- * What it computes (paper: Introduction, "the SDM Monte-Carlo algorithm for
- * representing collisional growth (Shima et al., 2009)"; API in brief, the
+ * What it computes (paper: Introduction, which names Shima et al.'s (2009)
+ * Monte-Carlo SDM scheme as the model of collisional growth; API in brief, the
  * Box(dt, dv) + Coalescence(Golovin(b)) example; Usage examples, Box
  * environment, the Golovin and Berry geometric sweep-out kernels).  The paper
  * names the algorithm but prints no formulae; the step below follows the
@@ -26,7 +26,7 @@
  * round-to-nearest and no contraction: build with -ffp-contract=off.
  *
  * Sedimentation (a next step of the method, paper: API in brief, the
- * "particle displacement" dynamic; Usage examples, the 2-D example's
+ * displacement of particles among the listed dynamics; Usage examples, the 2-D example's
  * sedimenting drizzle): every live SD falls by its Rogers-Yau fall speed
  * times dt.  Cells are levels x columns (cell = iz * nx + ix, levels of
  * height dz); an SD's position is its height zeta above its cell's bottom.
