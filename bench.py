@@ -494,7 +494,8 @@ def measure_kfp32(sdm, torch, g, steps=600):
     a, b = specs["fp64"], specs["kfp32"]
     out["spectrum_rel_l1_kfp32_vs_fp64"] = float(np.abs(b - a).sum() / np.abs(a).sum())
     out["steps"] = steps
-    out["note"] = "state resident, no L2 flush between steps (state 67 MB)"
+    out["note"] = ("one 600-step call per precision under the default launch tuning (fused launches of "
+                   f"{sdm.FUSE_STEPS_DEFAULT} steps); state resident, no L2 flush between steps (state 67 MB)")
     return out
 
 
@@ -529,11 +530,11 @@ def measure_serving(torch, n_requests=200):
     from paper_2103_17238_gb300 import serve
 
     reqs = I.serving_stream(n_requests=n_requests)
-    srv = serve.Server(budget_bytes=120 * 10**9, chunk=20)
+    srv = serve.Server(budget_bytes=120 * 10**9, chunk=20, fuse_steps=0)  # one launch per step
     res = srv.serve(reqs)
     out = {"workload": f"{n_requests} Poisson arrivals at 200/s (rng 4): Golovin boxes or geometric grids, "
                        "n_sd=round(2^U(10,20)), 100-1000 steps, dt in {0.5,1,2}; HBM budget 120 GB; "
-                       "ticks of up to 20 steps",
+                       "ticks of up to 20 steps, one launch per step",
            "pair_updates_per_s": res["pair_updates_per_s"], "step_latency_ms": res["step_latency_ms"],
            "time_in_system_s": res["time_in_system_s"], "requests": res["requests"],
            "max_active": res["max_active"], "wall_s": res["wall_s"]}

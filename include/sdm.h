@@ -248,13 +248,17 @@ typedef struct sdm_tuning {
     int32_t smem_max_sd;     /* largest cell sorted in shared memory: 512, 1024, 2048 or 4096 (default) */
     int32_t warp_cell_max;   /* largest cell run by one warp: 0, 64, 128, 256 or 512 (default), <= smem_max_sd */
     int32_t warps_per_block; /* warps per block of the warp-per-cell kernel: 1, 2 (default) or 4 */
-    int32_t fuse_steps;      /* 0 or 1 (default): one launch per step.  2..1024: the warp-per-cell
-                              * kernel keeps each cell in shared memory for up to fuse_steps
-                              * consecutive steps of one sdm_batch_step / sdm_coalescence_step call
-                              * (the same state, bit for bit: cells are independent, so a cell may
-                              * take its steps apart from the others); cells of other sizes still
-                              * take one launch per step.  A graph captures the same launches. */
+    int32_t fuse_steps;      /* 2..1024 (default SDM_FUSE_STEPS_DEFAULT): the warp-per-cell kernel
+                              * keeps each cell in shared memory for up to fuse_steps consecutive
+                              * steps of one sdm_batch_step / sdm_coalescence_step call (the same
+                              * state, bit for bit: cells are independent, so a cell may take its
+                              * steps apart from the others); cells of other sizes still take one
+                              * launch per step, and a one-step call is one launch either way.
+                              * 0 or 1: one launch per step for every cell.  A graph captures the
+                              * same launches. */
 } sdm_tuning;
+
+#define SDM_FUSE_STEPS_DEFAULT 64
 
 /* NULL restores the defaults.  Errors: SDM_EINVAL. */
 sdm_status sdm_set_tuning(const sdm_tuning *tuning);

@@ -361,7 +361,7 @@ constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
 int g_spec_grid = 1; // blocks of the total-spectrum kernel (resident blocks x SMs)
 
 std::mutex g_tuning_mutex;
-sdm_tuning g_tuning = {4096, 512, 2, 0};
+sdm_tuning g_tuning = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT};
 
 bool same_tuning(const sdm_tuning &a, const sdm_tuning &b)
 {
@@ -1395,7 +1395,7 @@ sdm_status sdm_batch_destroy(sdm_batch *batch)
 
 sdm_status sdm_set_tuning(const sdm_tuning *t)
 {
-    sdm_tuning v = {4096, 512, 2, 0};
+    sdm_tuning v = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT};
     if (t) {
         const bool smem_ok = t->smem_max_sd == 512 || t->smem_max_sd == 1024 || t->smem_max_sd == 2048 ||
                              t->smem_max_sd == 4096;

@@ -68,6 +68,9 @@ class sdm_config(ctypes.Structure):
     ]
 
 
+FUSE_STEPS_DEFAULT = 64  # SDM_FUSE_STEPS_DEFAULT of the header
+
+
 class sdm_tuning(ctypes.Structure):
     _fields_ = [
         ("smem_max_sd", ctypes.c_int32),
@@ -362,12 +365,13 @@ def sdm_get_positions(ctx, n_sd: int | None = None, z=None, cell=None, want_z: b
 
 def sdm_set_tuning(tuning=None):
     """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block and
-    optionally fuse_steps (default 0: one launch per step); None: defaults."""
+    optionally fuse_steps (absent: the default, FUSE_STEPS_DEFAULT steps per
+    fused launch; 0: one launch per step); None: defaults."""
     if tuning is None:
         _check(load().sdm_set_tuning(None), "sdm_set_tuning")
         return
     t = sdm_tuning(int(tuning["smem_max_sd"]), int(tuning["warp_cell_max"]), int(tuning["warps_per_block"]),
-                   int(tuning.get("fuse_steps", 0)))
+                   int(tuning.get("fuse_steps", FUSE_STEPS_DEFAULT)))
     _check(load().sdm_set_tuning(ctypes.byref(t)), "sdm_set_tuning")
 
 

@@ -6,9 +6,9 @@ memory: a request enters as soon as it has arrived and its footprint
 (``sdm_footprint_bytes``) fits in what the budget has left.  Admitted runs
 keep their state resident and advance together: at every tick the active set
 is stepped by one fused batch (``sdm_batch_step``) of ``chunk`` steps, capped
-so that no run overshoots its own length (with ``fuse_steps`` the tick's
-steps of every cell of up to 512 SDs run in one launch: the launch tuning's
-fused mode, same results).  Runs that finish hand back their
+so that no run overshoots its own length (``fuse_steps`` sets the launch
+tuning's fused mode for the batches: a tick's steps of every cell of up to
+512 SDs in one launch, or with 0 one launch per step; same results).  Runs that finish hand back their
 dv/dlnr spectrum and final state and leave; their memory admits the next
 ones.  Every run keeps its own seed and step counter, so its result is the
 same alone and in any mix.
@@ -55,21 +55,21 @@ def make_run(inst: I.Instance) -> sdm.Run:
 
 class Server:
     def __init__(self, budget_bytes: int, chunk: int = 20, keep_state: bool = False, use_graph: bool = False,
-                 time_scale: float = 1.0, fuse_steps: int = 0):
+                 time_scale: float = 1.0, fuse_steps: int | None = None):
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
-        self.fuse_steps = int(fuse_steps)  # 0: the process-wide tuning as it is
+        self.fuse_steps = fuse_steps  # None: the process-wide tuning as it is
         self.keep_state = keep_state
         self.use_graph = use_graph
         self.time_scale = time_scale  # arrival times are divided by this
 
     def _batch(self, runs):
         """A batch of the active runs; its launch plan takes the tuning of the
-        moment it is built, so fusion is switched on for that moment only."""
-        if self.fuse_steps < 2:
+        moment it is built, so the fusion setting applies for that moment only."""
+        if self.fuse_steps is None:
             return sdm.Batch(runs, use_graph=self.use_graph, graph_steps=self.chunk)
         prev = sdm.sdm_get_tuning()
-        sdm.sdm_set_tuning({**prev, "fuse_steps": self.fuse_steps})
+        sdm.sdm_set_tuning({**prev, "fuse_steps": int(self.fuse_steps)})
         try:
             return sdm.Batch(runs, use_graph=self.use_graph, graph_steps=self.chunk)
         finally:

@@ -91,18 +91,32 @@ def test_destroy_null_and_footprint(lib):
     assert big > 2**20 * 20 + 2**20 * 8  # state, then rank and perm per SD of a big cell
 
 
+def test_fuse_default_matches_the_header():
+    import re
+
+    from paper_2103_17238_gb300 import sdm
+
+    txt = open(os.path.join(ROOT, "include", "sdm.h")).read()
+    m = re.search(r"#define SDM_FUSE_STEPS_DEFAULT (\d+)", txt)
+    assert m and int(m.group(1)) == sdm.FUSE_STEPS_DEFAULT
+
+
 def test_tuning_round_trip_and_validation(lib):
     """The launch tuning is host state: set, read back, rejected when out of
     range (the previous setting stays), restored by NULL."""
     from paper_2103_17238_gb300 import sdm
 
-    default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": 0}
+    default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2,
+               "fuse_steps": sdm.FUSE_STEPS_DEFAULT}
     sdm.sdm_set_tuning(None)
     assert sdm.sdm_get_tuning() == default
-    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 0}
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": sdm.FUSE_STEPS_DEFAULT}
     sdm.sdm_set_tuning({k: t[k] for k in ("smem_max_sd", "warp_cell_max", "warps_per_block")})
     assert sdm.sdm_get_tuning() == t
     t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 1024}
+    sdm.sdm_set_tuning(t)
+    assert sdm.sdm_get_tuning() == t
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 0}
     sdm.sdm_set_tuning(t)
     assert sdm.sdm_get_tuning() == t
     for bad in ({"smem_max_sd": 8192, "warp_cell_max": 256, "warps_per_block": 2},

@@ -30,10 +30,11 @@ def _stream(n=14):
     return reqs
 
 
-@pytest.mark.parametrize("fuse", [0, 8])
+@pytest.mark.parametrize("fuse", [None, 0, 8])
 def test_served_equals_alone(env, fuse):
-    """Also with each tick's steps fused for the small cells; the tuning is
-    restored after every batch is built."""
+    """With the process-wide tuning, with one launch per step, and with each
+    tick's steps fused for the small cells; the tuning is restored after
+    every batch is built."""
     sdm, serve, torch = env
     reqs = _stream()
     fps = [serve.footprint(r.inst) for r in reqs]

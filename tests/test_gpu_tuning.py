@@ -19,6 +19,10 @@ SIZES = [0, 1, 2, 3, 31, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 102
 TUNINGS = [dict(smem_max_sd=s, warp_cell_max=w, warps_per_block=k)
            for s, w, k in itertools.product((512, 1024, 2048, 4096), (0, 64, 128, 256, 512), (1, 2, 4))
            if not (w == 0 and k != 2)]
+# every other setting with one launch per step, the rest with the default fusion
+for _i, _t in enumerate(TUNINGS):
+    if _i % 2:
+        _t["fuse_steps"] = 0
 
 
 @pytest.fixture(scope="module")
@@ -92,7 +96,7 @@ def test_autotuned_batch_equals_default(env, tmp_path):
     probe = make()
     rep = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert not rep["cached"] and rep["best"] in cands
-    assert sdm.sdm_get_tuning() == {"fuse_steps": 0, **rep["best"]}
+    assert sdm.sdm_get_tuning() == {"fuse_steps": sdm.FUSE_STEPS_DEFAULT, **rep["best"]}
     assert rep["ms_per_step"] <= rep["worst_ms_per_step"]
     again = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert again["cached"] and again["best"] == rep["best"]
