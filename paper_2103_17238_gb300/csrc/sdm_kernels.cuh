@@ -559,9 +559,12 @@ __device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cel
 // FUSED: every cell stays in its stage for n_fused consecutive steps (its
 // updates go to the stage, which returns to global memory at the end), for
 // runs whose steps have no other dynamic in between; cells are independent,
-// so this is the same sequence of steps per cell.  Otherwise one step.
+// so this is the same sequence of steps per cell.  Otherwise one step.  The
+// fused form of cells up to 256 SDs is bounded to 10 blocks of 2 warps per
+// SM (96 registers): a cell's load is rare there, so more warps beat the
+// few spills.
 template <int CAP, int WARPS, int STAGES, bool FUSED = false>
-__global__ void __launch_bounds__(32 * WARPS) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
+__global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
                                                                     InstDev *const *__restrict__ insts,
                                                                     int64_t step_offset, int32_t n_fused = 1)
 {

@@ -314,12 +314,13 @@ void launch_warp(int grid, int n, const WorkItem *items, InstDev *const *insts, 
 }
 
 // The fused form (every cell stays in shared memory for nf steps) always runs
-// 2 warps per block.
+// 2 warps per block, with one pipeline stage per warp: a warp loads a cell
+// once per nf steps, so a second stage would only cost shared memory.
 template <int CAP>
 void launch_warp_fused(int grid, int n, const WorkItem *items, InstDev *const *insts, int64_t off, int32_t nf,
                        cudaStream_t st)
 {
-    warp_cell_step_kernel<CAP, 2, 2, true><<<grid, 64, WarpSmem<CAP, 2>::per_warp * 2, st>>>(items, n, insts, off, nf);
+    warp_cell_step_kernel<CAP, 2, 1, true><<<grid, 64, WarpSmem<CAP, 1>::per_warp * 2, st>>>(items, n, insts, off, nf);
 }
 
 template <int CAP, int NT, int ST>
@@ -428,12 +429,12 @@ cudaError_t configure_kernels_once()
         v = 0;
 #define X(CAP)                                                                                                         \
     {                                                                                                                  \
-        const int bytes = (int)(WarpSmem<CAP, 2>::per_warp * 2);                                                       \
-        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, 2, 2, true>,                                          \
+        const int bytes = (int)(WarpSmem<CAP, 1>::per_warp * 2);                                                       \
+        if ((r = cudaFuncSetAttribute(warp_cell_step_kernel<CAP, 2, 1, true>,                                          \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)             \
             e = r;                                                                                                     \
         int per_sm = 0;                                                                                                \
-        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, 2, 2, true>, 64,    \
+        if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, 2, 1, true>, 64,    \
                                                                bytes)) != cudaSuccess)                                 \
             e = r;                                                                                                     \
         g_fused[v++].max_grid = std::max(1, per_sm) * sms;                                                             \
