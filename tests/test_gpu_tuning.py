@@ -163,3 +163,30 @@ def test_fused_grid_matches_the_oracle(env):
     finally:
         sdm.sdm_set_tuning(None)
     assert np.array_equal(gx, st.xi) and np.array_equal(gv, st.v)
+
+
+def test_fused_cells_that_die_out(env):
+    """Cells whose SDs coalesce away inside one fused launch: pairs of xi = 1
+    with p >> 1 split into a dead SD and a live one at the first step, so the
+    cell has n_c = 1 for the launch's later steps; larger cells of xi = 1 halve
+    their live count step after step.  Every state equals the oracle's."""
+    O, sdm, torch = env
+    sizes = [2, 3, 4, 5, 8, 17, 64, 255]
+    cell = np.concatenate([np.full(n, c, np.int32) for c, n in enumerate(sizes)])
+    n = len(cell)
+    xi = np.ones(n, np.int64)
+    v = np.full(n, 4 / 3 * np.pi * (50e-6) ** 3)
+    nc, dv, seed, steps = len(sizes), 1e-12, 41, 12  # Golovin with a tiny dV: p far above 1
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, nc)
+    O.run(O.params("golovin", "fp64", dv=dv, seed=seed), st, 0, steps)
+    assert (st.xi > 0).sum() < n // 2  # most SDs died
+    for fuse in (0, 12, 5):
+        sdm.sdm_set_tuning({"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": fuse})
+        try:
+            run = sdm.Run(sdm.make_config("golovin", "fp64", dv=dv, n_cells=nc, seed=seed), n)
+            run.set_attributes(xi, v, cell).step(steps)
+            gx, gv = run.attributes()
+            run.close()
+        finally:
+            sdm.sdm_set_tuning(None)
+        assert np.array_equal(gx, st.xi) and np.array_equal(gv, st.v), f"fuse_steps {fuse}"
