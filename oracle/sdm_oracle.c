@@ -35,7 +35,8 @@
  *
  * Parity status: every function below is pinned by tests/test_oracle_*.py
  * (Philox known answers, hand-worked Shima pairs, brute-force pairing and
- * gamma frequencies, volume conservation, the Golovin closed form).  The
+ * gamma frequencies in both precisions, binary32 hand cases of p, volume
+ * conservation, the Golovin closed form, hand-worked per-cell spectra).  The
  * geometric (Rogers-Yau) kernel has no closed form; it is pinned by
  * invariants only (symmetry, K(r,r) = 0, regime values, conservation).
  */

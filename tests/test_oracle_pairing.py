@@ -51,21 +51,49 @@ def test_unpaired_uniform_n3(oracle_lib):
     assert stats.chisquare(left[[0, 2, 3]]).pvalue > 1e-4
 
 
+def _kernel_independent(kernel, vi, vj, b=1500.0):
+    """K(i, j) written out from its definition in binary64 numpy, apart from
+    the oracle: Golovin b (v_i + v_j), or the geometric sweep-out
+    pi (r_i + r_j)^2 |v_t(r_i) - v_t(r_j)| with r = (3 v / 4 pi)^(1/3) and the
+    Rogers-Yau speeds k1 r^2 (r < 40 um), k2 r (r < 600 um), k3 sqrt(r)."""
+    if kernel == "golovin":
+        return b * (vi + vj)
+
+    def vt(r):
+        if r < 40e-6:
+            return 1.19e8 * r * r
+        if r < 600e-6:
+            return 8.0e3 * r
+        return 201.0 * math.sqrt(r)
+
+    ri, rj = (float(np.cbrt(3.0 * x / (4.0 * math.pi))) for x in (vi, vj))
+    return math.pi * (ri + rj) ** 2 * abs(vt(ri) - vt(rj))
+
+
+@pytest.mark.parametrize("kernel,precision", [("golovin", "fp64"), ("golovin", "kfp32"),
+                                              ("geometric", "fp64"), ("geometric", "kfp32")])
 @pytest.mark.parametrize("n_c", [2, 3, 8, 9])
-def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c):
+def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c, kernel, precision):
     """E[sum of gamma over the drawn pairs] = sum over ALL pairs i<j of
     K_ij max(xi_i, xi_j) dt/dV: the [n_c(n_c-1)/2]/floor(n_c/2) factor makes
     floor(n_c/2) random pairs stand for every pair.  Exact expectation by
-    brute force over pairs, versus the mean over 4000 one-step runs."""
+    brute force over pairs, versus the mean over 4000 one-step runs.  In
+    KFP32 mode K and p are binary32 (relative rounding below 1e-5 here,
+    added to the statistical band); a dropped scale, p taken with the smaller
+    multiplicity or a swapped operand in either precision's branch moves the
+    mean by far more than the band."""
     O = oracle_lib
     rng = np.random.default_rng(n_c)
+    # volumes spanning radii ~6 to ~60 um: the geometric kernel's Stokes and
+    # linear regimes both occur
     v = np.exp(rng.uniform(np.log(1e-15), np.log(1e-12), n_c))
     xi = rng.integers(10**6, 10**7, n_c).astype(np.int64)
-    # every p stays below 1/2: p <= b (2 v_max) xi_max n_c / dV
-    dv = 2.0 * 1500.0 * 2.0 * float(v.max()) * float(xi.max()) * n_c
-    P = O.params("golovin", b=1500.0, dt=1.0, dv=dv)
-    want = sum(1500.0 * (v[i] + v[j]) * max(xi[i], xi[j]) / dv
-               for i in range(n_c) for j in range(i + 1, n_c))
+    pairs = [(i, j) for i in range(n_c) for j in range(i + 1, n_c)]
+    kmax = max(_kernel_independent(kernel, v[i], v[j]) for i, j in pairs)
+    # every p stays below 1/2: p <= K_max xi_max n_c / dV
+    dv = 2.0 * kmax * float(xi.max()) * n_c
+    P = O.params(kernel, precision, b=1500.0, dt=1.0, dv=dv)
+    want = sum(_kernel_independent(kernel, v[i], v[j]) * max(xi[i], xi[j]) / dv for i, j in pairs)
     tot = 0
     runs = 4000
     for seed in range(runs):
@@ -74,7 +102,7 @@ def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c):
         tot += O.step(P, st, 0).sum_gamma
     mean = tot / runs
     # gamma per pair is Bernoulli(p) with p <= 1/2 here: variance <= want
-    assert abs(mean - want) < 5 * math.sqrt(want / runs)
+    assert abs(mean - want) < 5 * math.sqrt(want / runs) + 1e-5 * want
 
 
 def _tie_fixture():

@@ -76,6 +76,43 @@ def test_probability_golovin_value(oracle_lib):
     assert O.probability(P, sc, xij, vj, vk) == pytest.approx(want, rel=1e-15)
 
 
+def test_probability_kfp32_hand_case(oracle_lib):
+    """KFP32 mode: K and p in binary32 in the order (K xi_j) scale.  Dyadic
+    inputs make every binary32 operation exact: b = 2^10, v_j = 2^-40,
+    v_k = 2^-41, xi_j = 3 2^10, dt = 1, dV = 2^-10 and n_c = 2 (scale 2^10)
+    give K = 3 2^-31 and p = 9 2^-11 exactly, in both precisions."""
+    O = oracle_lib
+    for prec in ("fp64", "kfp32"):
+        P = O.params("golovin", prec, b=1024.0, dt=1.0, dv=2.0**-10)
+        sc = O.scale(P, 2)
+        assert sc == 1024.0
+        assert O.probability(P, sc, 3 * 1024, 2.0**-40, 2.0**-41) == 9 * 2.0**-11
+        # the multiplicity passed is the one that scales p (xi_j, the larger)
+        assert O.probability(P, sc, 1024, 2.0**-40, 2.0**-41) == 3 * 2.0**-11
+
+
+def test_probability_kfp32_rounds_each_operation_in_binary32(oracle_lib):
+    """Non-dyadic inputs: the KFP32 value is the binary32 evaluation of
+    (b (v_j + v_k) xi_j) scale from the binary32 images of its inputs, each
+    operation rounded once (numpy float32 arithmetic, which rounds every
+    operation to nearest), and differs from the binary64 value by rounding
+    only."""
+    O = oracle_lib
+    f = np.float32
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        vj, vk = np.exp(rng.uniform(np.log(1e-18), np.log(1e-9), 2))
+        xij = int(rng.integers(1, 2**40))
+        n_c = int(rng.integers(2, 5000))
+        P = O.params("golovin", "kfp32", b=1500.0, dt=1.0, dv=1e6 / 3)
+        sc = O.scale(P, n_c)
+        K = f(1500.0) * (f(vj) + f(vk))
+        want = float((K * f(xij)) * f(sc))
+        assert O.probability(P, sc, xij, vj, vk) == want
+        p64 = O.probability(O.params("golovin", "fp64", b=1500.0, dt=1.0, dv=1e6 / 3), sc, xij, vj, vk)
+        assert want == pytest.approx(p64, rel=4 * 2.0**-24)
+
+
 def test_cbrt_against_libm(oracle_lib):
     O = oracle_lib
     rng = np.random.default_rng(5)
