@@ -280,9 +280,13 @@ sdm_status sdm_get_tuning(sdm_tuning *out);
  *             and seed as for sdm_create; n_cells must be 1; step0 and the
  *             allocator hooks are ignored
  *   step      index of this step (>= 0); the random streams use cell index 0
- *   xi[n_sd]  int64 multiplicities, device memory, 16-byte aligned, SDs in
- *             rank order (the order that addresses their random keys)
- *   volume[n_sd]  binary64 volumes, device memory, 16-byte aligned
+ *   xi[n_sd]  int64 multiplicities, device (or managed) memory of the
+ *             current device, 16-byte aligned, SDs in rank order (the order
+ *             that addresses their random keys)
+ *   volume[n_sd]  binary64 volumes, the same kind of memory, 16-byte aligned
+ *             (both pointers are checked with cudaPointerGetAttributes, which
+ *             allocates nothing; a host pointer or another device's memory is
+ *             refused with SDM_EINVAL)
  *   n_sd      even, in [2, SDM_NOALLOC_MAX_SD]; pad an odd cell with one dead
  *             SD (xi = 0)
  *   cuda_stream   stream the work is ordered on (NULL: legacy default stream)
@@ -296,7 +300,9 @@ sdm_status sdm_get_tuning(sdm_tuning *out);
  * first call before any stream capture.  Every call shares the one array and
  * leaves its contents behind, so calls whose work overlaps on the GPU (two
  * streams, two host threads, two devices' calls aimed at one device) race:
- * order them on one stream.  Errors: SDM_EINVAL, SDM_ECUDA (message from
+ * order them on one stream.  Errors: SDM_EINVAL, SDM_ECUDA (also when a
+ * CUDA error from earlier work is pending on the calling thread: it is
+ * reported, not cleared, and nothing is launched; message from
  * sdm_last_error(NULL)). */
 #define SDM_NOALLOC_MAX_SD 1048576
 

@@ -13,6 +13,7 @@
 // Compiled as part of the library's single translation unit (included at the
 // end of sdm_runtime.cu), after the kernels it launches.
 
+#include <initializer_list>
 #include <mutex>
 
 namespace {
@@ -130,10 +131,36 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
                     (long long)n_sd, (long long)kNaMaxSd);
     if (!xi || !volume || ((uintptr_t)xi & 15) || ((uintptr_t)volume & 15))
         return fail(nullptr, SDM_EINVAL, "sdm_cell_step_noalloc: xi and volume must be 16-byte aligned device arrays");
+    // an error left by earlier, unrelated work on this thread is reported as
+    // such and left in place for its owner (the final check below would
+    // otherwise take it for this call's launch failure and clear it)
+    cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return fail(nullptr, SDM_ECUDA, "sdm_cell_step_noalloc: a CUDA error from earlier work is pending: %s",
+                    cudaGetErrorString(pending));
     unsigned char *base = nullptr;
     st = noalloc_base(&base);
     if (st != SDM_OK)
         return st;
+    // both arrays must be memory of the current device (a host pointer or
+    // another device's buffer would fault inside the kernels); the query
+    // allocates nothing
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (const void *ptr : {(const void *)xi, (const void *)volume}) {
+        cudaPointerAttributes a{};
+        const cudaError_t pe = cudaPointerGetAttributes(&a, ptr);
+        if (pe != cudaSuccess) {
+            cudaGetLastError(); // the query's own error, not a launch failure
+            return fail(nullptr, SDM_EINVAL, "sdm_cell_step_noalloc: pointer query failed: %s",
+                        cudaGetErrorString(pe));
+        }
+        if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != cur)
+            return fail(nullptr, SDM_EINVAL,
+                        "sdm_cell_step_noalloc: xi and volume must be device (or managed) memory of the current "
+                        "device %d",
+                        cur);
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     InstDev inst{};
     inst.xi = xi;

@@ -335,31 +335,51 @@ struct Variant {
     int cap;
     int warps; // warps per block of the warp kernel; 0: block kernel
     launch_fn launch;
-    int max_grid; // resident blocks x SMs (set at configuration)
 };
 
 // the fused warp kernels by capacity 64 .. 512
 struct FusedVariant {
     int cap;
     fused_fn launch;
-    int max_grid;
 };
-FusedVariant g_fused[] = {{64, launch_warp_fused<64>, 0},
-                          {128, launch_warp_fused<128>, 0},
-                          {256, launch_warp_fused<256>, 0},
-                          {512, launch_warp_fused<512>, 0}};
+const FusedVariant g_fused[] = {{64, launch_warp_fused<64>},
+                                {128, launch_warp_fused<128>},
+                                {256, launch_warp_fused<256>},
+                                {512, launch_warp_fused<512>}};
 
-Variant g_variants[] = {
-#define X(CAP, WARPS) {CAP, WARPS, launch_warp<CAP, WARPS>, 0},
+const Variant g_variants[] = {
+#define X(CAP, WARPS) {CAP, WARPS, launch_warp<CAP, WARPS>},
     SDM_WARP_VARIANTS(X)
 #undef X
-#define X(CAP, NT, ST) {CAP, 0, launch_block<CAP, NT, ST>, 0},
+#define X(CAP, NT, ST) {CAP, 0, launch_block<CAP, NT, ST>},
         SDM_BLOCK_VARIANTS(X)
 #undef X
 };
 constexpr int kNumVariants = sizeof(g_variants) / sizeof(g_variants[0]);
+constexpr int kNumFused = sizeof(g_fused) / sizeof(g_fused[0]);
+constexpr int kMaxDevices = 64;
 
-int g_spec_grid = 1; // blocks of the total-spectrum kernel (resident blocks x SMs)
+// Per-device launch set-up: the kernels' shared-memory limits are attributes
+// of each device's context, and the persistent grids are sized from that
+// device's SM count (resident blocks x SMs).
+struct DevGrids {
+    bool done = false;
+    cudaError_t status = cudaSuccess;
+    int variant[kNumVariants] = {};
+    int fused[kNumFused] = {};
+    int spec = 1; // blocks of the total-spectrum kernel
+};
+std::mutex g_dev_mutex;
+DevGrids g_dev[kMaxDevices];
+
+// The current device's table (configured by configure_kernels).
+const DevGrids &dev_grids()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        dev = 0;
+    return g_dev[dev];
+}
 
 std::mutex g_tuning_mutex;
 sdm_tuning g_tuning = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT};
@@ -388,13 +408,23 @@ int variant_for(int cap, const sdm_tuning &t)
     return -1;
 }
 
-cudaError_t configure_kernels_once()
+// Configures the current device once (the first context, batch or spectrum
+// call on each device does it, with that device current).
+cudaError_t configure_kernels()
 {
-    static cudaError_t status = [] {
-        cudaError_t e = cudaSuccess, r;
-        int dev = 0, sms = 0;
-        if ((r = cudaGetDevice(&dev)) != cudaSuccess)
-            return r;
+    int dev = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r != cudaSuccess)
+        return r;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_dev_mutex);
+    DevGrids &G = g_dev[dev];
+    if (G.done)
+        return G.status;
+    G.status = [&] {
+        cudaError_t e = cudaSuccess;
+        int sms = 0;
         if ((r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return r;
         int v = 0;
@@ -408,7 +438,7 @@ cudaError_t configure_kernels_once()
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, WARPS, 2>,          \
                                                                32 * WARPS, bytes)) != cudaSuccess)                     \
             e = r;                                                                                                     \
-        g_variants[v++].max_grid = std::max(1, per_sm) * sms;                                                          \
+        G.variant[v++] = std::max(1, per_sm) * sms;                                                                   \
     }
         SDM_WARP_VARIANTS(X)
 #undef X
@@ -422,7 +452,7 @@ cudaError_t configure_kernels_once()
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_step_kernel<CAP, NT, ST>, NT, bytes)) != \
             cudaSuccess)                                                                                               \
             e = r;                                                                                                     \
-        g_variants[v++].max_grid = std::max(1, per_sm) * sms;                                                          \
+        G.variant[v++] = std::max(1, per_sm) * sms;                                                                   \
     }
         SDM_BLOCK_VARIANTS(X)
 #undef X
@@ -437,7 +467,7 @@ cudaError_t configure_kernels_once()
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_cell_step_kernel<CAP, 2, 1, true>, 64,    \
                                                                bytes)) != cudaSuccess)                                 \
             e = r;                                                                                                     \
-        g_fused[v++].max_grid = std::max(1, per_sm) * sms;                                                             \
+        G.fused[v++] = std::max(1, per_sm) * sms;                                                                      \
     }
         X(64) X(128) X(256) X(512)
 #undef X
@@ -445,21 +475,22 @@ cudaError_t configure_kernels_once()
         if ((r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spec_per_sm, spectrum_total_kernel, kSpecTotNT, 0)) !=
             cudaSuccess)
             e = r;
-        g_spec_grid = std::max(1, spec_per_sm) * sms;
+        G.spec = std::max(1, spec_per_sm) * sms;
         const int hb = (int)big_hist_smem(kBigMaxLB);
         if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         return e;
     }();
-    return status;
+    G.done = true;
+    return G.status;
 }
 
 void launch_variant(int v, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
 {
     const Variant &x = g_variants[v];
     const int per_block = x.warps > 0 ? x.warps : 1;
-    const int grid = std::min((n + per_block - 1) / per_block, x.max_grid);
+    const int grid = std::min((n + per_block - 1) / per_block, dev_grids().variant[v]);
     x.launch(grid, n, items, insts, off, st);
 }
 
@@ -642,7 +673,7 @@ void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
             const Variant &x = g_variants[pl.variant[k]];
             if (x.warps > 0) {
                 const FusedVariant &fv = g_fused[k];
-                const int grid = std::min((pl.n_items[k] + 1) / 2, fv.max_grid);
+                const int grid = std::min((pl.n_items[k] + 1) / 2, dev_grids().fused[k]);
                 fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, m, st);
             } else {
                 for (int32_t j = 0; j < m; ++j)
@@ -699,7 +730,7 @@ sdm_status batch_init(sdm_batch *b, sdm_ctx *const *ctxs, int32_t n_ctx, cudaStr
     b->mem.use_hooks_of(ctxs[0]->mem, stream);
     b->use_graph = use_graph != 0;
     b->graph_steps = graph_steps > 0 ? graph_steps : 16;
-    cudaError_t e = configure_kernels_once();
+    cudaError_t e = configure_kernels();
     if (e != cudaSuccess)
         return cuda_fail(b, e, "kernel configuration");
     sdm_status st = build_plan(b);
@@ -1206,10 +1237,10 @@ sdm_status sdm_spectrum(sdm_ctx *ctx, const double *r_edges, int32_t n_edges, in
     const int32_t nb = n_edges - 1;
     const int64_t n_out = per_cell ? (int64_t)ctx->cfg.n_cells * nb : nb;
     cudaStream_t s = ctx->stream;
-    CTX_CUDA(ctx, configure_kernels_once());
+    CTX_CUDA(ctx, configure_kernels());
     // the total over all cells with few bins: the atomic-free kernel
     const bool total = !per_cell && nb <= kSpecTotMaxBins;
-    const int grid = g_spec_grid;
+    const int grid = dev_grids().spec;
     // edges, then dln[b] = ln e[b+1] - ln e[b] (host logarithms), in one copy
     std::vector<double> host_e(r_edges, r_edges + n_edges);
     for (int32_t b = 0; b < nb; ++b)

@@ -330,6 +330,14 @@ def sdm_cell_step_noalloc(cfg: sdm_config, step: int, xi, volume, stream: int):
         raise ValueError("xi and volume must be device tensors")
     if kx.data_ptr() != xi.data_ptr() or kv.data_ptr() != volume.data_ptr():
         raise ValueError("xi and volume must be contiguous (the step works in place)")
+    # the C call takes one length for both arrays and runs on the current
+    # device: a shorter volume array or another device's tensor would be
+    # accessed out of bounds there, so both are refused here
+    if volume.numel() != xi.numel() or xi.dim() != 1 or volume.dim() != 1:
+        raise ValueError("xi and volume must be 1-D with the same number of elements")
+    torch = _torch()
+    if xi.device != volume.device or xi.device.index != torch.cuda.current_device():
+        raise ValueError("xi and volume must both be on the current CUDA device")
     _check(load().sdm_cell_step_noalloc(ctypes.byref(cfg), int(step), px, pv, int(kx.shape[0]),
                                         ctypes.c_void_p(stream)), "sdm_cell_step_noalloc")
 

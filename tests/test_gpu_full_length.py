@@ -1,0 +1,173 @@
+"""Parity at the benchmark workloads' full size and length, and the paper's
+own Golovin setting against the closed form.
+
+The oracle runs on every host core here (cells and runs are independent, so
+it is split into pieces in spawned processes; ``oracle/parallel.py``).
+Multiplicities must match bit for bit and volumes exactly (the tolerance of
+the parity tests, 1e-12 relative, is reported on failure).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_17238_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import oracle as O
+    from oracle import parallel as PP
+    from paper_2103_17238_gb300 import build as B
+    from paper_2103_17238_gb300 import sdm
+
+    B.build()
+    O.build()
+    torch.cuda.set_device(0)
+    return O, PP, sdm, torch
+
+
+def _assert_same(gx, gv, ox, ov, what):
+    bad = np.nonzero(gx != ox)[0]
+    assert bad.size == 0, f"{what}: {bad.size} multiplicities differ, first at SD {bad[0]}"
+    rel = np.abs(gv - ov) / np.abs(ov)
+    assert rel.max() <= 1e-12, f"{what}: volume rel err {rel.max()}"
+    assert np.array_equal(gv, ov), f"{what}: volumes differ by at most {rel.max():.3g} relative"
+
+
+def test_full_grid_whole_run(env):
+    """The 128 x 128 x 256 geometric grid (4.19M SDs) for all 600 steps of its
+    run: once as 600 one-step calls (the launch configuration the benchmark
+    times: one launch per step) and once as one 600-step call under the
+    default tuning (fused launches), every SD against the oracle.  Late in
+    the run many pairs have p > 1 and land near an integer, where the
+    binary32 filter abstains and the exact path decides."""
+    O, PP, sdm, torch = env
+    g = I.grid_geometric(seed=0)
+    ox, ov = PP.run_cells(dict(kernel="geometric", dv=g.dv, seed=0), g.xi, g.v, g.cell, g.n_cells, 0, 600)
+    assert int((ox != g.xi).sum()) > g.n_sd // 2
+    for mode in ("one launch per step", "default tuning"):
+        run = sdm.Run(sdm.make_config("geometric", dv=g.dv, n_cells=g.n_cells, seed=0), g.n_sd)
+        run.set_attributes(g.xi, g.v, g.cell)
+        if mode == "one launch per step":
+            for _ in range(600):
+                run.step(1)
+        else:
+            run.step(600)
+        gx, gv = run.attributes()
+        assert run.info().step == 600
+        run.close()
+        _assert_same(gx, gv, ox, ov, f"full grid, 600 steps, {mode}")
+
+
+def test_every_ensemble_member(env):
+    """All 1024 members of the batched ensemble (n_sd = 2^U(8,16), 11.5M SDs)
+    for 24 steps in one batch replayed from a CUDA graph, each member against
+    the oracle run alone."""
+    O, PP, sdm, torch = env
+    insts = I.batched_ensemble(steps=24)
+    runs = [sdm.Run(sdm.make_config("golovin", "fp64", dv=t.dv, seed=t.seed), t.n_sd).set_attributes(t.xi, t.v, t.cell)
+            for t in insts]
+    batch = sdm.Batch(runs, use_graph=True, graph_steps=8)
+    batch.step(24)
+    torch.cuda.synchronize()
+    batch.close()
+    jobs = [(dict(kernel="golovin", dv=t.dv, seed=t.seed), t.xi, t.v, t.cell, 1, 0, 24) for t in insts]
+    want = PP.run_many(jobs)
+    changed = 0
+    for t, r, (ox, ov) in zip(insts, runs, want):
+        gx, gv = r.attributes()
+        r.close()
+        _assert_same(gx, gv, ox, ov, f"ensemble member n_sd={t.n_sd} seed={t.seed}")
+        changed += int((gx != t.xi).sum())
+    assert changed > 0
+
+
+def test_large_cells_fifty_steps(env):
+    """Two seeds of the 2^20-SD single cell (the large-cell workload) for 50
+    steps in one batch, the multi-pass global sort and pair path."""
+    O, PP, sdm, torch = env
+    gs = [I.box_golovin(2**20, seed=s) for s in (0, 1)]
+    runs = [sdm.Run(sdm.make_config("golovin", "fp64", dv=g.dv, seed=g.seed), g.n_sd).set_attributes(g.xi, g.v, g.cell)
+            for g in gs]
+    batch = sdm.Batch(runs)
+    batch.step(20).step(30)
+    torch.cuda.synchronize()
+    batch.close()
+    want = PP.run_many([(dict(kernel="golovin", dv=g.dv, seed=g.seed), g.xi, g.v, g.cell, 1, 0, 50) for g in gs])
+    for g, r, (ox, ov) in zip(gs, runs, want):
+        gx, gv = r.attributes()
+        r.close()
+        _assert_same(gx, gv, ox, ov, f"2^20 cell seed {g.seed}, 50 steps")
+        assert int((gx != g.xi).sum()) > 0
+
+
+def _golovin_ensemble(sdm, torch, n_sd, seeds, t_out):
+    """dv/dlnr and droplet number concentration of each seed's run at the
+    output times (the paper's Fig. 1 times), one batch of all seeds."""
+    runs = [sdm.Run(sdm.make_config("golovin", "fp64", dv=I.DV_BOX, seed=s), n_sd)
+            for s in seeds]
+    g = I.box_golovin(n_sd)
+    for r in runs:
+        r.set_attributes(g.xi, g.v, g.cell)
+    batch = sdm.Batch(runs, use_graph=True, graph_steps=100)
+    spec = {t: [] for t in t_out}
+    num = {t: [] for t in t_out}
+    done = 0
+    for t in t_out:
+        batch.step(t - done)
+        done = t
+        for r in runs:
+            spec[t].append(r.spectrum(I.R_EDGES))
+            num[t].append(r.diagnostics()["sum_xi"] / I.DV_BOX)
+    batch.close()
+    for r in runs:
+        r.close()
+    return spec, num
+
+
+def test_paper_setting_golovin_closed_form(env):
+    """The paper's Golovin box (API in brief, Fig. 1): n_sd = 2^17, dt = 1 s,
+    dV = 1e6 m^3, spectra at t = 1200, 2400 and 3600 s.  The ensemble mean
+    of 8 seeds is compared with the bin averages of the closed form
+    (relative L1 over bins holding >= 1e-3 of the peak) and N(t) with
+    N0 exp(-b N0 x0 t); the errors must be below those of the 2^12 box run
+    the same way, and the 2^17 run equals the oracle bit for bit over its
+    first 200 steps."""
+    from oracle import golovin as G
+
+    O, PP, sdm, torch = env
+    n_sd = 2**17
+    g = I.box_golovin(n_sd, seed=0)
+    run = sdm.Run(sdm.make_config("golovin", "fp64", dv=g.dv, seed=0), n_sd).set_attributes(g.xi, g.v, g.cell)
+    run.step(200)
+    gx, gv = run.attributes()
+    run.close()
+    st = O.State(g.xi.copy(), g.v.copy(), g.cell.copy(), None, 1)
+    O.run(O.params("golovin", dv=g.dv, seed=0), st, 0, 200)
+    _assert_same(gx, gv, st.xi, st.v, "2^17 box, first 200 steps")
+
+    t_out = [1200, 2400, 3600]
+    x0 = I.x0_box()
+    errs = {}
+    for n in (2**12, n_sd):
+        spec, num = _golovin_ensemble(sdm, torch, n, range(8), t_out)
+        for t in t_out:
+            want = G.dv_dlnr_bins(I.R_EDGES, t, b=I.GOLOVIN_B, n0=I.N_CONC_BOX, x0=x0)
+            mask = want >= 1e-3 * want.max()
+            mean = np.mean(spec[t], axis=0)
+            l1 = float(np.abs(mean[mask] - want[mask]).sum() / want[mask].sum())
+            n_want = G.total_number(t, b=I.GOLOVIN_B, n0=I.N_CONC_BOX, x0=x0)
+            got_n = np.array(num[t], dtype=np.float64)
+            se = got_n.std(ddof=1) / math.sqrt(len(got_n))
+            errs[(n, t)] = (l1, abs(got_n.mean() / n_want - 1.0))
+            assert abs(got_n.mean() - n_want) <= 3 * se + 0.04 * n_want, (n, t, got_n.mean(), n_want)
+    for t in t_out:
+        assert errs[(n_sd, t)][0] < 0.25, errs
+        assert errs[(n_sd, t)][0] < errs[(2**12, t)][0], errs

@@ -74,3 +74,37 @@ def test_noalloc_rejects_bad_sizes(env):
         sdm.sdm_cell_step_noalloc(cfg, 0, torch.ones(7, dtype=torch.int64, device=dev),
                                   torch.ones(7, dtype=torch.float64, device=dev), stream)
     assert e.value.status == sdm.SDM_EINVAL and "even" in str(e.value)
+    # a volume array shorter than xi is refused on the host, before any launch
+    with pytest.raises(ValueError):
+        sdm.sdm_cell_step_noalloc(cfg, 0, torch.ones(64, dtype=torch.int64, device=dev),
+                                  torch.ones(32, dtype=torch.float64, device=dev), stream)
+    # host memory handed to the C entry point directly is refused by its
+    # pointer check, before any launch
+    xi_h = torch.ones(64, dtype=torch.int64).pin_memory()
+    v_h = torch.ones(64, dtype=torch.float64).pin_memory()
+    rc = sdm.load().sdm_cell_step_noalloc(sdm.ctypes.byref(cfg), 0, sdm.ctypes.c_void_p(xi_h.data_ptr()),
+                                          sdm.ctypes.c_void_p(v_h.data_ptr()), 64, sdm.ctypes.c_void_p(stream))
+    assert rc == sdm.SDM_EINVAL
+
+
+def test_noalloc_allocates_no_device_memory(env):
+    """After a first call (the per-device set-up), further calls leave the
+    device's free memory and torch's allocator untouched."""
+    sdm, torch = env
+    dev = torch.device("cuda", 0)
+    n = 1 << 16
+    xi, v = _cell(n, 3)
+    cfg = sdm.make_config("geometric", dv=1e-2, n_cells=1, seed=3)
+    xi_d = torch.from_numpy(xi).to(dev)
+    v_d = torch.from_numpy(v).to(dev)
+    stream = sdm.current_stream_handle()
+    sdm.sdm_cell_step_noalloc(cfg, 0, xi_d, v_d, stream)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    alloc0 = torch.cuda.memory_allocated(dev)
+    for s in range(1, 6):
+        sdm.sdm_cell_step_noalloc(cfg, s, xi_d, v_d, stream)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert free1 == free0
