@@ -51,9 +51,13 @@ typedef enum {
  * environment examples -- the Golovin additive kernel, with its analytic
  * solution, and Berry's geometric sweep-out kernel). */
 typedef enum {
-    SDM_KERNEL_GOLOVIN = 0,  /* K = b (v_j + v_k) */
-    SDM_KERNEL_GEOMETRIC = 1 /* K = pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)|, E = 1,
-                                v_t from Rogers & Yau (1989), r = (3 v / 4 pi)^(1/3) */
+    SDM_KERNEL_GOLOVIN = 0,   /* K = b (v_j + v_k) */
+    SDM_KERNEL_GEOMETRIC = 1, /* K = pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)|, E = 1,
+                                 v_t from Rogers & Yau (1989), r = (3 v / 4 pi)^(1/3) */
+    SDM_KERNEL_LONG = 2       /* the geometric K times Long's (1974) collision
+                                 efficiency: with R = max(r_j, r_k), r = min(r_j, r_k),
+                                 E = max(4.5e8 R^2 (1 - 3e-6 / r), 1e-3) for R <= 50e-6 m,
+                                 E = 1 above (SI form of the published cgs constants) */
 } sdm_kernel;
 
 /* Precision of the kernel K and probability p.  Multiplicities are always

@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
 # at 40 um and 600 um.
 RY_DEFAULTS = dict(k1=1.19e8, k2=8.0e3, k3=201.0, r1=40.0e-6, r2=600.0e-6)
 
-KERNELS = {"golovin": 0, "geometric": 1}
+KERNELS = {"golovin": 0, "geometric": 1, "long": 2}
 PRECISIONS = {"fp64": 0, "kfp32": 1}
 
 
@@ -118,6 +118,10 @@ def lib():
             L.orc_kernel.restype = ctypes.c_double
             L.orc_kernelf.argtypes = [_P(Params), ctypes.c_float, ctypes.c_float]
             L.orc_kernelf.restype = ctypes.c_float
+            L.orc_efficiency_long.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_efficiency_long.restype = ctypes.c_double
+            L.orc_efficiency_longf.argtypes = [ctypes.c_float, ctypes.c_float]
+            L.orc_efficiency_longf.restype = ctypes.c_float
             L.orc_scale.argtypes = [_P(Params), ctypes.c_int64]
             L.orc_scale.restype = ctypes.c_double
             L.orc_probability.argtypes = [_P(Params), ctypes.c_double, ctypes.c_int64, ctypes.c_double, ctypes.c_double]
@@ -199,6 +203,14 @@ def kernel(P, vj, vk):
 
 def kernelf(P, vj, vk):
     return lib().orc_kernelf(ctypes.byref(P), float(vj), float(vk))
+
+
+def efficiency_long(rj, rk):
+    return lib().orc_efficiency_long(float(rj), float(rk))
+
+
+def efficiency_longf(rj, rk):
+    return lib().orc_efficiency_longf(float(rj), float(rk))
 
 
 def scale(P, n_c):

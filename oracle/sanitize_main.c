@@ -6,7 +6,7 @@
  *
  * Cases: layouts of 1 to 37 cells in 1 or 2 instances with empty, single-SD
  * and large cells, dead SDs, multiplicities up to 2^62, SDs outside the
- * domain, both collision kernels in both precisions, p far below and far
+ * domain, all three collision kernels in both precisions, p far below and far
  * above 1; total and per-cell spectra; sedimentation steps; the permutation
  * and the pair-level functions; and rejected layouts.  Exits non-zero on an
  * unexpected status or a broken conservation law (sum xi v kept to 1e-12,
@@ -173,7 +173,7 @@ static void run_case(int case_id, int32_t n_cells, int32_t n_inst, int32_t max_p
 int main(void)
 {
     int id = 0;
-    for (int32_t kernel = 0; kernel < 2; ++kernel)
+    for (int32_t kernel = 0; kernel < 3; ++kernel)
         for (int32_t precision = 0; precision < 2; ++precision) {
             run_case(id++, 1, 1, 4096, kernel, precision, 1e6, 0);
             run_case(id++, 37, 1, 300, kernel, precision, 1e3, 1);

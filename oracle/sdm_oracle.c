@@ -50,7 +50,8 @@
 #define ORC_ENOMEM 2
 
 typedef struct {
-    int32_t kernel;    /* 0: Golovin additive, 1: geometric sweep-out (Rogers-Yau v_t) */
+    int32_t kernel;    /* 0: Golovin additive, 1: geometric sweep-out (Rogers-Yau v_t),
+                          2: geometric sweep-out times Long's (1974) collision efficiency */
     int32_t precision; /* 0: K and p in binary64; 1: K and p in binary32 */
     double b;          /* Golovin constant, s^-1 */
     double dt;         /* timestep, s */
@@ -268,15 +269,50 @@ float orc_vtf(const orc_params *P, float r)
     return (float)P->k3 * sqrtf(r);
 }
 
-/* K(j,k) in m^3 s^-1: Golovin b (v_j + v_k), or geometric sweep-out
- * pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)| with collection efficiency 1. */
+/* Collision efficiency of Long (1974, J. Atmos. Sci. 31, 1040-1052), the
+ * form later SDM studies use for their hydrodynamic ("Long") kernel: with
+ * R the larger and r the smaller radius of the pair,
+ *   E = max(c1 R^2 (1 - c2 / r), E_min)   for R <= R_lim,
+ *   E = 1                                 for R >  R_lim,
+ * c1 = 4.5e4 cm^-2 = 4.5e8 m^-2, c2 = 3e-4 cm = 3e-6 m, E_min = 1e-3,
+ * R_lim = 50 um.  (The form reaches 1.0575 at R = r = 50 um; it is used as
+ * published, without a cap at 1.)  Binary64, in this operation order. */
+double orc_efficiency_long(double rj, double rk)
+{
+    double R = rj > rk ? rj : rk;
+    double r = rj > rk ? rk : rj;
+    if (R > 50e-6)
+        return 1.0;
+    double e = (4.5e8 * (R * R)) * (1.0 - 3e-6 / r);
+    return e < 1e-3 ? 1e-3 : e;
+}
+
+/* The same in binary32, with the binary32 roundings of the binary64
+ * constants. */
+float orc_efficiency_longf(float rj, float rk)
+{
+    float R = rj > rk ? rj : rk;
+    float r = rj > rk ? rk : rj;
+    if (R > (float)50e-6)
+        return 1.0f;
+    float e = ((float)4.5e8 * (R * R)) * (1.0f - (float)3e-6 / r);
+    return e < (float)1e-3 ? (float)1e-3 : e;
+}
+
+/* K(j,k) in m^3 s^-1: Golovin b (v_j + v_k) (kernel 0); geometric sweep-out
+ * pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)| with collection efficiency 1
+ * (kernel 1); the same sweep-out times Long's efficiency E(r_j, r_k)
+ * (kernel 2). */
 double orc_kernel(const orc_params *P, double vj, double vk)
 {
     if (P->kernel == 0)
         return P->b * (vj + vk);
     double rj = orc_radius(vj), rk = orc_radius(vk);
     double s = rj + rk;
-    return (ORC_PI * (s * s)) * fabs(orc_vt(P, rj) - orc_vt(P, rk));
+    double K = (ORC_PI * (s * s)) * fabs(orc_vt(P, rj) - orc_vt(P, rk));
+    if (P->kernel == 2)
+        K = K * orc_efficiency_long(rj, rk);
+    return K;
 }
 
 float orc_kernelf(const orc_params *P, float vj, float vk)
@@ -285,7 +321,10 @@ float orc_kernelf(const orc_params *P, float vj, float vk)
         return (float)P->b * (vj + vk);
     float rj = orc_radiusf(vj), rk = orc_radiusf(vk);
     float s = rj + rk;
-    return ((float)ORC_PI * (s * s)) * fabsf(orc_vtf(P, rj) - orc_vtf(P, rk));
+    float K = ((float)ORC_PI * (s * s)) * fabsf(orc_vtf(P, rj) - orc_vtf(P, rk));
+    if (P->kernel == 2)
+        K = K * orc_efficiency_longf(rj, rk);
+    return K;
 }
 
 /* dt/dV * [n_c(n_c-1)/2] / floor(n_c/2): the factor that rescales the pair

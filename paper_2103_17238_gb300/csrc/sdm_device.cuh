@@ -17,7 +17,7 @@
 
 namespace sdm {
 
-enum : int32_t { KERNEL_GOLOVIN = 0, KERNEL_GEOMETRIC = 1 };
+enum : int32_t { KERNEL_GOLOVIN = 0, KERNEL_GEOMETRIC = 1, KERNEL_LONG = 2 };
 enum : int32_t { PREC_FP64 = 0, PREC_KFP32 = 1 };
 
 // Per-run parameters, one record per context in device memory.
@@ -230,6 +230,35 @@ __device__ __forceinline__ double vt_exact(const InstDev &P, double r)
     return __dmul_rn(P.k3, __dsqrt_rn(r));
 }
 
+// ------------------------------------------------ Long's collision efficiency
+// Long (1974): with R the larger and r the smaller radius of the pair,
+// E = max(c1 R^2 (1 - c2 / r), E_min) for R <= R_lim and 1 above, with
+// c1 = 4.5e8 m^-2, c2 = 3e-6 m, E_min = 1e-3, R_lim = 50 um (the cgs
+// constants 4.5e4 cm^-2 and 3e-4 cm in SI).  The kernel is the geometric
+// sweep-out times E.  Both precisions use the binary64 constants' values
+// (binary32: their roundings), in this operation order.
+constexpr double kLongC1 = 4.5e8, kLongC2 = 3e-6, kLongEmin = 1e-3, kLongRlim = 50e-6;
+constexpr float kLongC1F = (float)kLongC1, kLongC2F = (float)kLongC2, kLongEminF = (float)kLongEmin,
+                kLongRlimF = (float)kLongRlim;
+
+__device__ __forceinline__ double efficiency_long_exact(double rj, double rk)
+{
+    const double R = rj > rk ? rj : rk, r = rj > rk ? rk : rj;
+    if (R > kLongRlim)
+        return 1.0;
+    const double e = __dmul_rn(__dmul_rn(kLongC1, __dmul_rn(R, R)), __dsub_rn(1.0, __ddiv_rn(kLongC2, r)));
+    return e < kLongEmin ? kLongEmin : e;
+}
+
+__device__ __forceinline__ float efficiency_long32(float rj, float rk)
+{
+    const float R = rj > rk ? rj : rk, r = rj > rk ? rk : rj;
+    if (R > kLongRlimF)
+        return 1.0f;
+    const float e = __fmul_rn(__fmul_rn(kLongC1F, __fmul_rn(R, R)), __fsub_rn(1.0f, __fdiv_rn(kLongC2F, r)));
+    return e < kLongEminF ? kLongEminF : e;
+}
+
 // --------------------------------------------------------------- p and gamma
 // Exact binary64 probability (the definition).
 __device__ __noinline__ double probability_exact(const InstDev &P, double scale, int64_t xi_j, double vj,
@@ -242,6 +271,8 @@ __device__ __noinline__ double probability_exact(const InstDev &P, double scale,
         const double rj = radius_exact(vj), rk = radius_exact(vk);
         const double s = __dadd_rn(rj, rk);
         K = __dmul_rn(__dmul_rn(kPi, __dmul_rn(s, s)), fabs(__dsub_rn(vt_exact(P, rj), vt_exact(P, rk))));
+        if (P.kernel == KERNEL_LONG)
+            K = __dmul_rn(K, efficiency_long_exact(rj, rk));
     }
     return __dmul_rn(__dmul_rn(K, __ll2double_rn(xi_j)), scale);
 }
@@ -421,9 +452,24 @@ __device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float 
         const float tj = vt_guarded(C, rj, ok), tk = vt_guarded(C, rk, ok);
         const float s = rj + rk;
         const float a = kPiF * (s * s);
-        const float K = a * fabsf(tj - tk);
+        float K = a * fabsf(tj - tk);
+        float km = a * (tj + tk);
+        if (C.kernel == KERNEL_LONG) {
+            // E and Em = c1 R^2 (1 + c2 / r) + E_min >= E: the error of the
+            // filter's E is below 2^-16.9 Em (radii 2^-18.8, the quotient
+            // 2^-21 with the approximate division, products), so K's bound
+            // becomes (2^-16.4 + 2^-16.9) km Em < 2^-15.6 km Em, and E below
+            // stays over 5 times the total.  Abstains within 2^-14 of R_lim.
+            const float R = fmaxf(rj, rk), r = fminf(rj, rk);
+            ok &= !(R > kLongRlimF * (1.0f - 0x1p-14f) && R < kLongRlimF * (1.0f + 0x1p-14f));
+            if (R <= kLongRlimF) {
+                const float c = kLongC1F * (R * R);
+                const float q = __fdividef(kLongC2F, r);
+                K *= fmaxf(c * (1.0f - q), kLongEminF);
+                km *= c * (1.0f + q) + kLongEminF;
+            }
+        }
         pf = (K * xjf) * sc;
-        const float km = a * (tj + tk);
         mag = (km * xjf) * sc;
         ok &= km >= 0x1p-126f && (K == 0.0f || K >= 0x1p-126f);
     }
@@ -441,6 +487,8 @@ __device__ __forceinline__ int32_t pair_gamma_filter(const PairConsts &C, float 
 
 // A bound that settles most pairs before the filter: gamma = 0 is certain
 // when p < u, and p <= B xi_j scale.  Golovin: K = b (v_j + v_k) <= 2 b v_max.
+// Long: the geometric bound below times 1.125 >= Long's E (at most
+// c1 R_lim^2), folded into pre_c on the host.
 // Geometric: the fall speed never decreases with r (the Rogers-Yau regimes
 // join with upward steps), so K = pi (r_j + r_k)^2 |v_t(r_j) - v_t(r_k)| <=
 // 4 pi r_max^2 v_t(r_max), which in each regime is
@@ -525,6 +573,8 @@ __device__ __forceinline__ int64_t pair_gamma_exact(const InstDev *P, uint32_t n
             const float rj = radius32(vjf), rk = radius32(vkf);
             const float s = __fadd_rn(rj, rk);
             K = __fmul_rn(__fmul_rn(kPiF, __fmul_rn(s, s)), fabsf(__fsub_rn(vt32c(C, rj), vt32c(C, rk))));
+            if (C.kernel == KERNEL_LONG)
+                K = __fmul_rn(K, efficiency_long32(rj, rk));
         }
         p = (double)__fmul_rn(__fmul_rn(K, xjf), scale_f);
     } else {

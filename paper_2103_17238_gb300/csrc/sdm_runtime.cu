@@ -828,7 +828,7 @@ sdm_status check_config(const sdm_config *cfg, std::string *err)
 {
     if (!cfg)
         return fail(err, SDM_EINVAL, "config is NULL");
-    if (cfg->kernel != SDM_KERNEL_GOLOVIN && cfg->kernel != SDM_KERNEL_GEOMETRIC)
+    if (cfg->kernel != SDM_KERNEL_GOLOVIN && cfg->kernel != SDM_KERNEL_GEOMETRIC && cfg->kernel != SDM_KERNEL_LONG)
         return fail(err, SDM_EINVAL, "unknown kernel %d", cfg->kernel);
     if (cfg->precision != SDM_PREC_FP64 && cfg->precision != SDM_PREC_KFP32)
         return fail(err, SDM_EINVAL, "unknown precision %d", cfg->precision);
@@ -863,9 +863,11 @@ void set_prefilter(InstDev &d)
         d.pre_c[0] = up(2.0 * d.b);
         d.pre_c[1] = d.pre_c[2] = d.pre_c[0];
     } else {
-        d.pre_c[0] = up(4.0 * pi * d.k1 * std::pow(0.75 / pi, 4.0 / 3.0));
-        d.pre_c[1] = up(3.0 * d.k2);
-        d.pre_c[2] = up(4.0 * pi * d.k3 * std::pow(0.75 / pi, 5.0 / 6.0));
+        // Long's efficiency never exceeds c1 R_lim^2 = 1.125
+        const double e = d.kernel == SDM_KERNEL_LONG ? 1.125 : 1.0;
+        d.pre_c[0] = up(4.0 * pi * d.k1 * std::pow(0.75 / pi, 4.0 / 3.0) * e);
+        d.pre_c[1] = up(3.0 * d.k2 * e);
+        d.pre_c[2] = up(4.0 * pi * d.k3 * std::pow(0.75 / pi, 5.0 / 6.0) * e);
     }
     d.pre_v[0] = down(4.0 / 3.0 * pi * d.r1 * d.r1 * d.r1);
     d.pre_v[1] = down(4.0 / 3.0 * pi * d.r2 * d.r2 * d.r2);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsdm.so")
 
 SDM_OK, SDM_EINVAL, SDM_ENOMEM, SDM_ECUDA, SDM_ESTATE, SDM_ETIMEOUT, SDM_EBUDGET = range(7)
 STATUS_NAMES = ["SDM_OK", "SDM_EINVAL", "SDM_ENOMEM", "SDM_ECUDA", "SDM_ESTATE", "SDM_ETIMEOUT", "SDM_EBUDGET"]
-KERNELS = {"golovin": 0, "geometric": 1}
+KERNELS = {"golovin": 0, "geometric": 1, "long": 2}
 PRECISIONS = {"fp64": 0, "kfp32": 1}
 
 # every symbol include/sdm.h declares

@@ -66,6 +66,24 @@ def test_full_grid_whole_run(env):
         _assert_same(gx, gv, ox, ov, f"full grid, 600 steps, {mode}")
 
 
+@pytest.mark.parametrize("precision", ["fp64", "kfp32"])
+def test_full_grid_long_kernel(env, precision):
+    """The full grid with Long's collision efficiency on the geometric
+    kernel, 60 one-step calls, every SD against the oracle."""
+    O, PP, sdm, torch = env
+    g = I.grid_geometric(seed=1)
+    ox, ov = PP.run_cells(dict(kernel="long", precision=precision, dv=g.dv, seed=1), g.xi, g.v, g.cell,
+                          g.n_cells, 0, 60)
+    run = sdm.Run(sdm.make_config("long", precision, dv=g.dv, n_cells=g.n_cells, seed=1), g.n_sd)
+    run.set_attributes(g.xi, g.v, g.cell)
+    for _ in range(60):
+        run.step(1)
+    gx, gv = run.attributes()
+    run.close()
+    _assert_same(gx, gv, ox, ov, f"full grid, Long kernel, {precision}")
+    assert int((gx != g.xi).sum()) > 0
+
+
 def test_every_ensemble_member(env):
     """All 1024 members of the batched ensemble (n_sd = 2^U(8,16), 11.5M SDs)
     for 24 steps in one batch replayed from a CUDA graph, each member against

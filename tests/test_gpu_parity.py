@@ -73,7 +73,7 @@ def test_box_golovin_full_run(env):
     run.close()
 
 
-@pytest.mark.parametrize("kernel", ["golovin", "geometric"])
+@pytest.mark.parametrize("kernel", ["golovin", "geometric", "long"])
 @pytest.mark.parametrize("precision", ["fp64", "kfp32"])
 def test_grid(env, kernel, precision):
     O, sdm, torch = env
@@ -125,7 +125,8 @@ def _ragged_state(rng, sizes, p_scale):
 
 @pytest.mark.parametrize("kernel,precision,dv", [("golovin", "fp64", 1e3), ("geometric", "fp64", 1e3),
                                                  ("geometric", "kfp32", 1e3), ("golovin", "fp64", 1e-3),
-                                                 ("geometric", "fp64", 1e-4)])
+                                                 ("geometric", "fp64", 1e-4), ("long", "fp64", 1e3),
+                                                 ("long", "kfp32", 1e-4)])
 def test_ragged_cells_every_class(env, kernel, precision, dv):
     """Every shared-memory size class, its edges, empty/odd/tiny cells and the
     big-cell path; dead SDs, equal and extreme multiplicities; unsorted
@@ -142,7 +143,7 @@ def test_ragged_cells_every_class(env, kernel, precision, dv):
     run.close()
 
 
-@pytest.mark.parametrize("kernel", ["golovin", "geometric"])
+@pytest.mark.parametrize("kernel", ["golovin", "geometric", "long"])
 @pytest.mark.parametrize("precision", ["fp64", "kfp32"])
 def test_probability_sweep(env, kernel, precision):
     """p from ~1e-3 to ~1e3 (dV over six decades): gamma = 0, 1, several,
@@ -181,6 +182,39 @@ def test_terminal_velocity_regime_edges(env):
         gx, gv = run.attributes()
         st = _oracle_run(O, "geometric", prec, xi, v, cell, 8, 1e-3, 21, 6)
         _assert_same(gx, gv, st, f"regime edges {prec}")
+        run.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "kfp32"])
+def test_long_efficiency_edges(env, precision):
+    """Long's efficiency where the binary32 filter must abstain or is near
+    its bound: collector radii within a few ulp of 50 um (the switch to
+    E = 1), collected radii near 3 um (1 - c2 / r cancels to the 1e-3
+    floor), near-equal radii (the speed difference cancels), across the
+    warp, block and multi-pass size classes."""
+    O, sdm, torch = env
+    rng = np.random.default_rng(31)
+    n_each = 700
+    r = np.concatenate([
+        50e-6 * (1 + rng.uniform(-1e-6, 1e-6, n_each)),
+        3e-6 * (1 + rng.uniform(-1e-3, 1e-3, n_each)),
+        30e-6 * (1 + rng.uniform(-1e-7, 1e-7, n_each)),
+        np.exp(rng.uniform(np.log(1e-6), np.log(2e-4), 3 * n_each)),
+    ])
+    v = 4 / 3 * np.pi * r**3
+    n = len(v)
+    xi = rng.integers(1, 10**6, n).astype(np.int64)
+    sizes = [64, 200, 256, 500, 1000, 2000]
+    cell = np.concatenate([np.full(k, c, np.int32) for c, k in enumerate(sizes)])
+    cell = np.concatenate([cell, np.full(n - len(cell), len(sizes), np.int32)])  # one 5200-SD cell
+    perm = rng.permutation(n)
+    xi, v, cell = xi[perm], v[perm], cell[perm]
+    for dv in (1e-2, 1e-5):
+        run = _gpu_run(sdm, "long", precision, xi, v, cell, len(sizes) + 1, dv, 77, 6, chunks=[2, 4])
+        gx, gv = run.attributes()
+        st = _oracle_run(O, "long", precision, xi, v, cell, len(sizes) + 1, dv, 77, 6)
+        _assert_same(gx, gv, st, f"Long edges {precision} dv={dv}")
+        assert int((gx != xi).sum()) > 0
         run.close()
 
 

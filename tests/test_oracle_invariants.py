@@ -15,10 +15,11 @@ def _state(O, inst):
 
 
 @pytest.mark.parametrize("kernel,precision", [("golovin", "fp64"), ("geometric", "fp64"),
-                                              ("geometric", "kfp32"), ("golovin", "kfp32")])
+                                              ("geometric", "kfp32"), ("golovin", "kfp32"),
+                                              ("long", "fp64"), ("long", "kfp32")])
 def test_conservation_and_monotone_number(oracle_lib, kernel, precision):
     O = oracle_lib
-    inst = I.grid_geometric(side=4, sd_per_cell=64) if kernel == "geometric" else I.box_golovin(512)
+    inst = I.grid_geometric(side=4, sd_per_cell=64) if kernel != "golovin" else I.box_golovin(512)
     P = O.params(kernel, precision, dv=inst.dv)
     st = _state(O, inst)
     vol0 = math.fsum(st.xi * st.v)

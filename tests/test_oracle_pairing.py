@@ -67,11 +67,23 @@ def _kernel_independent(kernel, vi, vj, b=1500.0):
         return 201.0 * math.sqrt(r)
 
     ri, rj = (float(np.cbrt(3.0 * x / (4.0 * math.pi))) for x in (vi, vj))
-    return math.pi * (ri + rj) ** 2 * abs(vt(ri) - vt(rj))
+    k = math.pi * (ri + rj) ** 2 * abs(vt(ri) - vt(rj))
+    if kernel == "long":
+        k *= _long_efficiency_cgs(max(ri, rj) * 100.0, min(ri, rj) * 100.0)
+    return k
+
+
+def _long_efficiency_cgs(R, r):
+    """Long's (1974) collision efficiency in its published cgs form (radii in
+    cm): max(4.5e4 R^2 (1 - 3e-4 / r), 1e-3) for R <= 50 um, else 1."""
+    if R > 50e-4:
+        return 1.0
+    return max(4.5e4 * R * R * (1.0 - 3e-4 / r), 1e-3)
 
 
 @pytest.mark.parametrize("kernel,precision", [("golovin", "fp64"), ("golovin", "kfp32"),
-                                              ("geometric", "fp64"), ("geometric", "kfp32")])
+                                              ("geometric", "fp64"), ("geometric", "kfp32"),
+                                              ("long", "fp64"), ("long", "kfp32")])
 @pytest.mark.parametrize("n_c", [2, 3, 8, 9])
 def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c, kernel, precision):
     """E[sum of gamma over the drawn pairs] = sum over ALL pairs i<j of
@@ -85,7 +97,7 @@ def test_expected_collisions_equal_mean_field_rate(oracle_lib, n_c, kernel, prec
     O = oracle_lib
     rng = np.random.default_rng(n_c)
     # volumes spanning radii ~6 to ~60 um: the geometric kernel's Stokes and
-    # linear regimes both occur
+    # linear regimes both occur, and Long's efficiency on both sides of 50 um
     v = np.exp(rng.uniform(np.log(1e-15), np.log(1e-12), n_c))
     xi = rng.integers(10**6, 10**7, n_c).astype(np.int64)
     pairs = [(i, j) for i in range(n_c) for j in range(i + 1, n_c)]

@@ -113,6 +113,56 @@ def test_probability_kfp32_rounds_each_operation_in_binary32(oracle_lib):
         assert want == pytest.approx(p64, rel=4 * 2.0**-24)
 
 
+# Long (1974) collision efficiency by hand from its published cgs form
+# E = max(4.5e4 R^2 (1 - 3e-4 / r), 1e-3) for R <= 50 um (R, r in cm), else 1:
+# (R, r) in um -> E
+LONG_HAND = [
+    ((50.0, 10.0), 4.5e4 * 25e-6 * 0.7),        # 0.7875
+    ((20.0, 10.0), 4.5e4 * 4e-6 * 0.7),         # 0.126
+    ((30.0, 6.0), 4.5e4 * 9e-6 * 0.5),          # 0.2025
+    ((50.0, 50.0), 4.5e4 * 25e-6 * 0.94),       # 1.0575: the published form exceeds 1 here
+    ((40.0, 2.0), 1e-3),                        # 1 - 3e-4 / r < 0: the floor
+    ((10.0, 3.0), 1e-3),                        # r = 3 um: 1 - c2 / r = 0 exactly
+    ((50.001, 10.0), 1.0),                      # above 50 um
+    ((600.0, 100.0), 1.0),
+]
+
+
+@pytest.mark.parametrize("case", LONG_HAND)
+def test_long_efficiency_hand_values(oracle_lib, case):
+    O = oracle_lib
+    (R, r), want = case
+    R, r = R * 1e-6, r * 1e-6
+    assert O.efficiency_long(R, r) == pytest.approx(want, rel=1e-14)
+    assert O.efficiency_long(r, R) == O.efficiency_long(R, r)  # symmetric in the pair
+    assert O.efficiency_longf(R, r) == pytest.approx(want, rel=2e-6)
+
+
+def test_long_kernel_is_geometric_times_efficiency(oracle_lib):
+    """K_Long = E(r_j, r_k) K_geometric in both precisions (one extra
+    rounded product), E within (1e-3, 1.125]: never above 4.5e8 R_lim^2."""
+    O = oracle_lib
+    Pg, Pl = O.params("geometric"), O.params("long")
+    Pgf, Plf = O.params("geometric", "kfp32"), O.params("long", "kfp32")
+    rng = np.random.default_rng(8)
+    for _ in range(300):
+        vj, vk = np.exp(rng.uniform(np.log(1e-18), np.log(1e-8), 2))
+        rj, rk = O.radius(vj), O.radius(vk)
+        e = O.efficiency_long(rj, rk)
+        assert 1e-3 <= e <= 1.125
+        assert O.kernel(Pl, vj, vk) == O.kernel(Pg, vj, vk) * e
+        assert O.kernel(Pl, vk, vj) == O.kernel(Pl, vj, vk)
+        kf = O.kernelf(Plf, vj, vk)
+        # binary32 rounding relative to the magnitude of the terms (the speed
+        # difference and 1 - c2 / r can cancel)
+        R, r = max(rj, rk), min(rj, rk)
+        em = 1.0 if R > 50e-6 else 4.5e8 * R * R * (1 + 3e-6 / r) + 1e-3
+        mag = math.pi * (rj + rk) ** 2 * (O.vt(Pg, rj) + O.vt(Pg, rk)) * em
+        assert abs(kf - O.kernel(Pl, vj, vk)) <= 1e-5 * mag + 1e-30
+        assert O.kernelf(Pgf, vj, vk) * O.efficiency_longf(np.float32(O.radius(vj)), np.float32(O.radius(vk))) \
+            == pytest.approx(kf, rel=1e-5, abs=1e-30)
+
+
 def test_cbrt_against_libm(oracle_lib):
     O = oracle_lib
     rng = np.random.default_rng(5)
