@@ -52,7 +52,8 @@ WORKLOAD = ("grid_geometric: 128x128 cells x 256 SDs (4,194,304 SDs), dV=1e3 m^3
 KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
-EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "fused", "serving", "sedimentation")
+EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "fused", "serving", "sedimentation", "long_kernel",
+          "paper_setting")
 
 
 # The step kernel and every helper it uses: the device header, and the kernel
@@ -285,6 +286,10 @@ def run_ours(args, rank: int, world: int):
             extras["serving"] = measure_serving(torch, args.serve_requests)
         if "sedimentation" in wanted:
             extras["sedimentation"] = measure_sedimentation(sdm, torch, g)
+        if "long_kernel" in wanted:
+            extras["long_kernel"] = measure_long_kernel(sdm, torch, g)
+        if "paper_setting" in wanted:
+            extras["paper_setting"] = measure_paper_setting(sdm, torch)
     res = None
     if rank == 0:
         res = {
@@ -537,6 +542,78 @@ def measure_fused(sdm, torch, g, steps=600):
                 out[key + "_state_identical"] = bool(np.array_equal(xi, ref[0]) and np.array_equal(v, ref[1]))
     finally:
         sdm.sdm_set_tuning(None)
+    return out
+
+
+def measure_long_kernel(sdm, torch, g, steps=200):
+    """The grid with Long's (1974) collision efficiency on the geometric
+    kernel: one launch per step with L2 flushed between steps (as the
+    headline), FP64 and KFP32."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush_r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+    pairs = pairs_per_step(g.xi, g.cell, g.n_cells)
+    out = {"workload": "grid_geometric 4,194,304 SDs, geometric sweep-out x Long (1974) efficiency, first "
+                       f"{steps} steps, one launch per step, L2 flushed between steps", "steps": steps}
+    for prec in ("fp64", "kfp32"):
+        run = sdm.Run(sdm.make_config("long", prec, dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+        run.set_attributes(g.xi, g.v, g.cell).step(0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            torch.sum(flush_r, dim=0, out=sink)
+            a.record()
+            run.step(1)
+            b.record()
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        xi, _ = run.attributes()
+        run.close()
+        out[prec] = {"pair_updates_per_s": pairs / (ms * 1e-3), "ms_per_step": ms,
+                     "sds_changed": int((xi != g.xi).sum())}
+    return out
+
+
+def measure_paper_setting(sdm, torch, seeds=8):
+    """The paper's Golovin box (API in brief, Fig. 1): n_sd = 2^17 (and 2^12
+    for comparison), dt = 1 s, 3600 steps, 8 seeds in one batch; relative L1
+    error of the ensemble-mean dv/dlnr against the closed form's bin averages
+    (bins holding >= 1e-3 of the peak) and N(t) / N_closed_form - 1 at
+    t = 1200, 2400, 3600 s.  Time: the batch's 3600 steps (CUDA events)."""
+    from oracle import golovin as G
+
+    t_out = [1200, 2400, 3600]
+    x0 = I.x0_box()
+    out = {"workload": "Golovin box b=1500 s^-1, dV=1e6 m^3, dt=1 s, 3600 steps, 8 seeds batched", "seeds": seeds}
+    for n_sd in (2**12, 2**17):
+        g = I.box_golovin(n_sd)
+        runs = [sdm.Run(sdm.make_config("golovin", "fp64", dv=I.DV_BOX, seed=s), n_sd).set_attributes(g.xi, g.v, g.cell)
+                for s in range(seeds)]
+        batch = sdm.Batch(runs, use_graph=True, graph_steps=100)
+        done, step_s = 0, 0.0
+        res = {}
+        live = [seeds * n_sd]  # live SDs at 0 and at each output time
+        for t in t_out:
+            step_s += _timed(torch, lambda: batch.step(t - done))
+            done = t
+            spec = np.mean([r.spectrum(I.R_EDGES) for r in runs], axis=0)
+            diags = [r.diagnostics() for r in runs]
+            live.append(sum(d["live_sd"] for d in diags))
+            num = np.mean([d["sum_xi"] / I.DV_BOX for d in diags])
+            want = G.dv_dlnr_bins(I.R_EDGES, t, b=I.GOLOVIN_B, n0=I.N_CONC_BOX, x0=x0)
+            mask = want >= 1e-3 * want.max()
+            res[f"t{t}"] = {"spectrum_rel_l1": float(np.abs(spec[mask] - want[mask]).sum() / want[mask].sum()),
+                            "number_rel_err": float(num / G.total_number(t, b=I.GOLOVIN_B, n0=I.N_CONC_BOX,
+                                                                         x0=x0) - 1.0)}
+        batch.close()
+        for r in runs:
+            r.close()
+        res["ms_per_step"] = step_s / 3600 * 1e3
+        # pairs per step from the live counts at the output times (trapezoid)
+        pairs = sum(0.5 * (a + b) / 2 * (t1 - t0) for a, b, t0, t1 in zip(live[:-1], live[1:], [0] + t_out[:-1], t_out))
+        res["pair_updates_per_s"] = pairs / step_s
+        out[f"n_sd_2^{int(round(math.log2(n_sd)))}"] = res
     return out
 
 
