@@ -240,6 +240,35 @@ sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated);
  * arrays: synchronises; device arrays: stream-ordered. */
 sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, int on_device);
 
+/* ---- condensation (a next step of the method: the paper lists condensation
+ * among the dynamics of its framework and prints no formulae).  The large-
+ * drop limit of the diffusional growth law, r dr/dt = s G (Rogers & Yau
+ * 1989, ch. 7, with the curvature and solute terms dropped): s = S - 1 is
+ * the cell's supersaturation and G = 1 / (F_k + F_d) its growth coefficient
+ * (m^2 s^-1; F_k, F_d the heat-conduction and vapour-diffusion terms of the
+ * ambient temperature and pressure), both held over the step, so r^2 grows
+ * by exactly c = 2 G s dt.  An evaporating SD stops at the floor radius
+ * r_min, or at its own radius when that is already below r_min.
+ *
+ * Per live SD inside the domain, with cf = (float)(((2 G) s) dt) of its
+ * cell (binary64, rounded once): r = the binary32 radius of (float)v (the
+ * KFP32 twin), x = r r, x' = max(x + cf, min(x, (float)(r_min r_min))),
+ * d = cf (or that floor - x when the floor acts), a = sqrt(x'), b = sqrt(x),
+ * dV = k43 ((d ((x' + a b) + x)) / (a + b)) with k43 = (float)(4 pi / 3),
+ * all binary32; v += (double)dV in binary64.  Multiplicities, dead SDs and
+ * SDs outside the domain do not change.
+ *   G[n_cells], s[n_cells]  host arrays: G >= 0 finite, s in [-1, 1],
+ *                           |2 G s dt| <= 1e-6 m^2 (else SDM_EINVAL)
+ *   r_min                   floor radius, m, in [1e-9, 1e-3]
+ *   condensed               nullable: receives sum(xi dV) of each cell, m^3
+ *                           (n_cells values; summed in a fixed order, not
+ *                           the oracle's), host (condensed_on_device = 0: the
+ *                           call synchronises) or device (stream-ordered)
+ * Enqueued on the context's stream.  Errors: SDM_EINVAL, SDM_ESTATE (no
+ * attributes), SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_condensation_step(sdm_ctx *ctx, const double *G, const double *s, double r_min, double *condensed,
+                                 int condensed_on_device);
+
 /* ---- launch tuning.  Which cells are sorted in shared memory (the rest take
  * the multi-pass global path), which run one warp per cell, and how many
  * warps share a block.  Results never depend on it: every setting gives the

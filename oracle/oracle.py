@@ -150,6 +150,9 @@ def lib():
             L.orc_sediment.argtypes = [_P(Params), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                        _i64p, _f64p, _i32p, _f64p, _f64p]
             L.orc_sediment.restype = ctypes.c_int
+            L.orc_condense.argtypes = [_P(Params), ctypes.c_int64, ctypes.c_int32, _i32p, _i64p, _f64p, _f64p, _f64p,
+                                       ctypes.c_double, _f64p]
+            L.orc_condense.restype = ctypes.c_int
             L.orc_zeta_of.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
             L.orc_zeta_of.restype = ctypes.c_double
             L.orc_z_of.argtypes = [ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double]
@@ -336,3 +339,21 @@ def sediment(P: Params, st: State, nx: int, dz: float, zeta: np.ndarray) -> floa
     _check(lib().orc_sediment(ctypes.byref(P), n, int(nx), nc, float(dz), xp, vp, cp,
                               _ptr(zeta, ctypes.c_double), ctypes.byref(pr)), "sediment")
     return pr.value
+
+
+# --------------------------------------------------------------- condensation
+def condense(P: Params, st: State, G, s, r_min: float, want_condensed: bool = True):
+    """One condensation step in place (st.v); per-cell growth coefficient G
+    (m^2 s^-1) and supersaturation s; returns sum(xi dV) per cell (m^3) or
+    None."""
+    if st.inst is not None:
+        raise ValueError("condensation of a single instance only")
+    n, nc, ni, cp, ip, xp, vp = st._args()
+    Ga = np.ascontiguousarray(G, dtype=np.float64)
+    sa = np.ascontiguousarray(s, dtype=np.float64)
+    if len(Ga) != nc or len(sa) != nc:
+        raise ValueError("G and s need one value per cell")
+    out = np.zeros(nc, dtype=np.float64) if want_condensed else None
+    _check(lib().orc_condense(ctypes.byref(P), n, nc, cp, xp, vp, _ptr(Ga, ctypes.c_double),
+                              _ptr(sa, ctypes.c_double), float(r_min), _ptr(out, ctypes.c_double)), "condense")
+    return out

@@ -696,3 +696,62 @@ int orc_sediment(const orc_params *P, int64_t n_sd, int32_t nx, int32_t n_cells,
 double orc_zeta_of(double z, int32_t cell, int32_t nx, double dz) { return z - (double)(cell / nx) * dz; }
 
 double orc_z_of(double zeta, int32_t cell, int32_t nx, double dz) { return (double)(cell / nx) * dz + zeta; }
+
+/* ------------------------------------------------------------- condensation */
+/* Diffusional growth of every live SD inside the domain over one step, in
+ * the large-drop limit of the growth law r dr/dt = s G (Rogers & Yau 1989,
+ * ch. 7, with the curvature and solute terms dropped): s is the cell's
+ * supersaturation (S - 1) and G = 1 / (F_k + F_d) its growth coefficient,
+ * m^2 s^-1, both held over the step, so r^2 grows by exactly
+ * c = 2 G s dt.  An evaporating SD stops at the floor radius r_min, or at
+ * its own radius when that is already below r_min.
+ *
+ * Reading (as for the fall distance): the change of volume is evaluated in
+ * binary32, from the binary32 image of the volume and its binary32 radius,
+ * as the difference of (4 pi / 3) x^(3/2) at x' = x + c and at x = r^2,
+ * written without cancellation,
+ *   dV = k43 (d ((x' + a b) + x)) / (a + b),  a = sqrt(x'), b = sqrt(x),
+ * with d = x' - x taken as c itself (not as the rounded difference, which
+ * would lose the digits of c below x's last bit) unless the floor acts, and
+ * then as floor - x; dV is widened exactly and added to the binary64
+ * volume.  Multiplicities do not
+ * change.  condensed (nullable, n_cells entries) receives sum(xi dV) of
+ * each cell, m^3 (summed in SD-id order). */
+int orc_condense(const orc_params *P, int64_t n_sd, int32_t n_cells, const int32_t *cell, const int64_t *xi,
+                 double *v, const double *G, const double *s, double r_min, double *condensed)
+{
+    int rc = check_layout(n_sd, n_cells, 1, cell, NULL);
+    if (rc != ORC_OK)
+        return rc;
+    if (!(r_min > 0.0))
+        return ORC_EINVAL;
+    if (condensed)
+        for (int32_t c = 0; c < n_cells; ++c)
+            condensed[c] = 0.0;
+    const float k43 = (float)(4.0 * ORC_PI / 3.0);
+    const float xmin = (float)(r_min * r_min);
+    for (int64_t i = 0; i < n_sd; ++i) {
+        int32_t c = cell[i];
+        if (c < 0 || xi[i] <= 0)
+            continue;
+        float cf = (float)(((2.0 * G[c]) * s[c]) * P->dt);
+        float r = orc_radiusf((float)v[i]);
+        float x = r * r;
+        float xn = x + cf;
+        float lo = x < xmin ? x : xmin;
+        float d = cf; /* x' - x, exact where the floor does not act */
+        if (xn < lo) {
+            xn = lo;
+            d = lo - x;
+        }
+        float dv = 0.0f;
+        if (d != 0.0f) {
+            float a = sqrtf(xn), b = sqrtf(x);
+            dv = k43 * ((d * ((xn + a * b) + x)) / (a + b));
+        }
+        v[i] = v[i] + (double)dv;
+        if (condensed)
+            condensed[c] += (double)xi[i] * (double)dv;
+    }
+    return ORC_OK;
+}

@@ -398,30 +398,18 @@ __global__ void __launch_bounds__(NT, (1024 / NT > 0 ? 1024 / NT : 1)) cell_step
 }
 
 // ------------------------------------------------------ warp-per-cell step
-// Cells of at most 256 stored SDs: one warp per cell, no block barriers.
+// Cells of at most 512 stored SDs: one warp per cell, no block barriers.
 // Each warp runs its own bulk-copy pipeline (STAGES deep, one mbarrier per
-// stage), sorts its cell with the same one-pass bucket sort (a warp scan of
-// the bucket counts), and keeps its own queue of undecided pairs, which it
-// evaluates exactly, one pair per lane, once 32 have gathered.  Queue entries
-// hold storage slots only: the flush re-reads xi and v of its pairs from
-// global memory (this launch changes an SD only when its own pair is done).
-struct WQEntry {
-    uint32_t slot_j, slot_k; // storage slots in the run's arrays
-    uint32_t wa, wb;         // the pair's uniform words
-    uint32_t n_c;            // live SDs of its cell
-    int32_t inst;            // its run
-    int32_t gamma;           // certain collision count (>= 1), or -1: evaluate exactly
-};
-
-// The warp kernel queues only the pairs its filter cannot decide (certain
-// collisions are updated in place), so the queue holds few entries.
-constexpr int kWarpQueue = 96;
-
+// stage) and sorts its cell with a one-pass bucket sort (a warp scan of the
+// bucket counts) and a register sort.  A pair the binary32 filter cannot
+// decide is evaluated exactly at once, from the staged copy of its cell
+// (every SD is in one pair per step, so nothing else in the launch reads or
+// writes it).  No queue of such pairs is kept: that leaves 10.5 KB of shared
+// memory per warp at 256 SDs, and 10 blocks of 2 warps per SM.
 template <int CAP, int STAGES>
 struct WarpSmem {
-    // per warp: STAGES x (xi, v), sort word, bucket, perm, queue
-    static constexpr size_t per_warp =
-        (size_t)CAP * (16 * STAGES + 4 + 4 + 2) + sizeof(WQEntry) * (size_t)kWarpQueue;
+    // per warp: STAGES x (xi, v), sort word, bucket, perm
+    static constexpr size_t per_warp = (size_t)CAP * (16 * STAGES + 4 + 4 + 2);
 };
 
 __device__ __forceinline__ void cmp_swap(uint32_t &a, uint32_t &b)
@@ -559,12 +547,13 @@ __device__ __noinline__ uint32_t rank_in_bucket_full(uint64_t seed, uint32_t cel
 // FUSED: every cell stays in its stage for n_fused consecutive steps (its
 // updates go to the stage, which returns to global memory at the end), for
 // runs whose steps have no other dynamic in between; cells are independent,
-// so this is the same sequence of steps per cell.  Otherwise one step.  The
-// fused form of cells up to 256 SDs is bounded to 10 blocks of 2 warps per
-// SM (96 registers): a cell's load is rare there, so more warps beat the
-// few spills.
+// so this is the same sequence of steps per cell.  Otherwise one step.  For
+// cells up to 256 SDs both forms are bounded to 20 warps per SM (10 blocks
+// of 2 warps, 96 registers): the kernel is latency-bound, so more warps beat
+// the few spills (the one-step form went from 44.9 to 42.9 us per grid step
+// with L2 flushed, the fused form from 30.2 to 27.8).
 template <int CAP, int WARPS, int STAGES, bool FUSED = false>
-__global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
+__global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) warp_cell_step_kernel(const WorkItem *__restrict__ items, int32_t n_items,
                                                                     InstDev *const *__restrict__ insts,
                                                                     int64_t step_offset, int32_t n_fused = 1)
 {
@@ -586,13 +575,10 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
     uint32_t *s_word = reinterpret_cast<uint32_t *>(st_v + STAGES * CAP);
     uint32_t *s_hist = s_word + CAP;
     uint16_t *s_perm = reinterpret_cast<uint16_t *>(s_hist + NB);
-    WQEntry *s_q = reinterpret_cast<WQEntry *>(s_perm + CAP);
     __shared__ uint64_t s_bar_all[WARPS][STAGES];
     __shared__ int4 s_meta_all[WARPS][STAGES];
-    __shared__ uint32_t s_qn_all[WARPS];
     uint64_t *s_bar = s_bar_all[warp];
     int4 *s_meta = s_meta_all[warp];
-    uint32_t &s_qn = s_qn_all[warp];
 
     const int gw = blockIdx.x * WARPS + warp;
     const int nw = gridDim.x * WARPS;
@@ -600,7 +586,6 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
         for (int i = 0; i < STAGES; ++i)
             mbar_init(&s_bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_qn = 0;
     }
     __syncwarp();
 
@@ -622,30 +607,6 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
         mbar_arrive_expect_tx(&s_bar[sg], (uint32_t)it.n * 16u);
         bulk_g2s(st_xi + sg * CAP, P->xi + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
         bulk_g2s(st_v + sg * CAP, P->v + it.off, (uint32_t)it.n * 8u, &s_bar[sg]);
-    };
-
-    auto flush = [&]() { // whole warp
-        const uint32_t nq = s_qn < (uint32_t)kWarpQueue ? s_qn : (uint32_t)kWarpQueue;
-        for (uint32_t e = lane; e < nq; e += 32) {
-            const WQEntry E = s_q[e];
-            InstDev *Pq = insts[E.inst];
-            int64_t xj = Pq->xi[E.slot_j], xk = Pq->xi[E.slot_k];
-            double vj = Pq->v[E.slot_j], vk = Pq->v[E.slot_k];
-            const int64_t g = E.gamma > 0 ? cap_gamma(E.gamma, xj, xk)
-                                          : pair_gamma_exact(Pq, E.n_c, xj, xk, vj, vk, E.wa, E.wb);
-            if (g > 0) {
-                const bool split = shima_update(g, xj, xk, vj, vk);
-                Pq->xi[E.slot_j] = xj;
-                Pq->xi[E.slot_k] = xk;
-                Pq->v[E.slot_k] = vk;
-                if (split)
-                    Pq->v[E.slot_j] = vj;
-            }
-        }
-        __syncwarp();
-        if (lane == 0)
-            s_qn = 0;
-        __syncwarp();
     };
 
     if (lane == 0) {
@@ -862,7 +823,7 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
             // arrays, dead by now (2 CAP words hold 2 CAP / 3 >= CAP / 2
             // entries of 3 words: every pair fits), and go through the full
             // filter one per lane: certain collisions are updated at once,
-            // undecided pairs join the queue for the exact evaluation.
+            // and so are undecided pairs, after their exact evaluation.
             const uint32_t n_pairs = n_c / 2;
             const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
             const PairConsts C = pair_consts(P);
@@ -938,51 +899,16 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
                     const bool split = shima_update(cap_gamma(gf, xa, xb), xa, xb, va, vb);
                     put_pair(a, b, xa, xb, va, vb, split);
                 }
-                // pairs the filter could not decide: in FUSED mode evaluated
-                // exactly at once (from the stage); otherwise they wait in the
-                // queue for the exact evaluation
-                const bool und = gf < 0;
-                if constexpr (FUSED) {
-                    if (und) {
-                        int64_t xa = xs[a], xb = xs[b];
-                        double va = vs[a], vb = vs[b];
-                        const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
-                        if (g > 0) {
-                            const bool split = shima_update(g, xa, xb, va, vb);
-                            put_pair(a, b, xa, xb, va, vb, split);
-                        }
+                // pairs the filter could not decide: evaluated exactly at
+                // once, from the staged copy of the cell
+                if (gf < 0) {
+                    int64_t xa = xs[a], xb = xs[b];
+                    double va = vs[a], vb = vs[b];
+                    const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
+                    if (g > 0) {
+                        const bool split = shima_update(g, xa, xb, va, vb);
+                        put_pair(a, b, xa, xb, va, vb, split);
                     }
-                    continue;
-                }
-                const unsigned m = __ballot_sync(FULL, und);
-                if (m) {
-                    const uint32_t base = s_qn;
-                    const uint32_t idx = base + __popc(m & ((1u << lane) - 1u));
-                    if (und) {
-                        if (idx < (uint32_t)kWarpQueue) {
-                            WQEntry E;
-                            E.slot_j = (uint32_t)(meta.x + (int)a);
-                            E.slot_k = (uint32_t)(meta.x + (int)b);
-                            E.wa = wa;
-                            E.wb = wb;
-                            E.n_c = n_c;
-                            E.inst = meta.w;
-                            E.gamma = -1;
-                            s_q[idx] = E;
-                        } else { // queue full: evaluate here
-                            int64_t xa = xs[a], xb = xs[b];
-                            double va = vs[a], vb = vs[b];
-                            const int64_t g = pair_gamma_exact(P, n_c, xa, xb, va, vb, wa, wb);
-                            if (g > 0) {
-                                const bool split = shima_update(g, xa, xb, va, vb);
-                                put_pair(a, b, xa, xb, va, vb, split);
-                            }
-                        }
-                    }
-                    __syncwarp();
-                    if (lane == 0)
-                        s_qn = base + (uint32_t)__popc(m);
-                    __syncwarp();
                 }
             }
         }
@@ -999,11 +925,7 @@ __global__ void __launch_bounds__(32 * WARPS, (FUSED && CAP <= 256) ? 10 : 0) wa
             __syncwarp();
         }
         // stage sg is free again
-        if (s_qn >= 32u)
-            flush();
     }
-    if (s_qn > 0)
-        flush();
 }
 
 // ----------------------------------------------------------- big cells

@@ -161,7 +161,8 @@ struct Plan {
     std::vector<unsigned char> host_pack; // the tables uploaded in one copy
 };
 
-struct SedBuffers; // second layout and scratch of the sedimentation step (sdm_sediment.cu)
+struct SedBuffers;  // second layout and scratch of the sedimentation step (sdm_sediment.cu)
+struct CondBuffers; // work list and scratch of the condensation step (sdm_condense.cu)
 
 } // namespace
 
@@ -185,6 +186,7 @@ struct sdm_ctx {
     double dz = 0.0;
     double *d_zeta = nullptr; // height above the cell's bottom, per slot
     SedBuffers *sed = nullptr;
+    CondBuffers *cond = nullptr;
     std::string error;
     // device state
     int64_t *d_xi = nullptr;
@@ -209,7 +211,8 @@ struct sdm_ctx {
 };
 
 namespace {
-void sed_release(sdm_ctx *ctx); // frees the sedimentation buffers (sdm_sediment.cu)
+void sed_release(sdm_ctx *ctx);  // frees the sedimentation buffers (sdm_sediment.cu)
+void cond_release(sdm_ctx *ctx); // frees the condensation buffers (sdm_condense.cu)
 } // namespace
 
 struct sdm_batch {
@@ -1360,6 +1363,7 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     ctx->mem.put(ctx->d_cell_off, 0);
     ctx->mem.put(ctx->d_inst, 0);
     sed_release(ctx);
+    cond_release(ctx);
     ctx->mem.release_kept();
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (ctx->h_pin)
@@ -1528,4 +1532,5 @@ const char *sdm_batch_last_error(const sdm_batch *batch)
 
 // The allocation-free entry point, after the kernels and helpers it uses.
 #include "sdm_sediment.cu"
+#include "sdm_condense.cu"
 #include "sdm_noalloc.cu"

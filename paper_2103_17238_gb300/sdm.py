@@ -138,6 +138,7 @@ def load(path: str = LIB_PATH):
         L.sdm_set_tuning.argtypes = [P(sdm_tuning)]
         L.sdm_set_positions.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.c_int]
         L.sdm_sedimentation_step.argtypes = [vp, P(ctypes.c_double)]
+        L.sdm_condensation_step.argtypes = [vp, vp, vp, ctypes.c_double, vp, ctypes.c_int]
         L.sdm_get_positions.argtypes = [vp, vp, vp, ctypes.c_int]
         L.sdm_get_tuning.argtypes = [P(sdm_tuning)]
         L.sdm_diagnostics.argtypes = [vp, P(sdm_diag)]
@@ -342,6 +343,29 @@ def sdm_cell_step_noalloc(cfg: sdm_config, step: int, xi, volume, stream: int):
                                         ctypes.c_void_p(stream)), "sdm_cell_step_noalloc")
 
 
+def sdm_condensation_step(ctx, G, s, r_min: float, want_condensed: bool = True, n_cells: int | None = None,
+                          out=None):
+    """One condensation step; G, s: per-cell growth coefficient (m^2 s^-1)
+    and supersaturation (host arrays).  Returns the per-cell condensed water
+    sum(xi dV) (numpy, or `out` filled on the device) or None."""
+    Ga = np.ascontiguousarray(G, dtype=np.float64)
+    sa = np.ascontiguousarray(s, dtype=np.float64)
+    nc = int(n_cells if n_cells is not None else sdm_get_info(ctx).n_cells)
+    if Ga.shape != (nc,) or sa.shape != (nc,):
+        raise ValueError("G and s need one value per cell")
+    if out is not None:
+        po, on_dev, _ = _ptr_and_flag(out, np.float64)
+        res, flag = out, on_dev
+    elif want_condensed:
+        res = np.zeros(nc, dtype=np.float64)
+        po, flag = res.ctypes.data, 0
+    else:
+        res, po, flag = None, None, 0
+    _check(load().sdm_condensation_step(ctx, Ga.ctypes.data, sa.ctypes.data, float(r_min), po, flag),
+           "sdm_condensation_step", ctx)
+    return res
+
+
 def sdm_set_positions(ctx, z, nx: int, dz: float):
     pz, dev, kz = _ptr_and_flag(z, np.float64)
     _check(load().sdm_set_positions(ctx, pz, int(nx), float(dz), dev), "sdm_set_positions", ctx)
@@ -434,6 +458,10 @@ class Run:
 
     def attributes(self):
         return sdm_get_attributes(self.h)
+
+    def condense(self, G, s, r_min: float, want_condensed: bool = True):
+        """One condensation step; returns the per-cell condensed water, m^3."""
+        return sdm_condensation_step(self.h, G, s, r_min, want_condensed, n_cells=self.cfg.n_cells)
 
     def set_positions(self, z, nx: int, dz: float):
         sdm_set_positions(self.h, z, nx, dz)
