@@ -30,7 +30,7 @@ EXPORTS = [
     "sdm_get_attributes", "sdm_get_info", "sdm_footprint_bytes", "sdm_destroy", "sdm_last_error",
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
     "sdm_cell_step_noalloc", "sdm_set_tuning", "sdm_get_tuning",
-    "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions",
+    "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions", "sdm_condensation_step",
     "sdm_diagnostics", "sdm_selftest_bounded_wait",
 ]
 NOALLOC_MAX_SD = 1 << 20
