@@ -53,7 +53,7 @@ KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
 EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "fused", "serving", "sedimentation", "long_kernel",
-          "paper_setting")
+          "paper_setting", "condensation")
 
 
 # The step kernel and every helper it uses: the device header, and the kernel
@@ -290,6 +290,8 @@ def run_ours(args, rank: int, world: int):
             extras["long_kernel"] = measure_long_kernel(sdm, torch, g)
         if "paper_setting" in wanted:
             extras["paper_setting"] = measure_paper_setting(sdm, torch)
+        if "condensation" in wanted:
+            extras["condensation"] = measure_condensation(sdm, torch, g)
     res = None
     if rank == 0:
         res = {
@@ -572,6 +574,46 @@ def measure_long_kernel(sdm, torch, g, steps=200):
         run.close()
         out[prec] = {"pair_updates_per_s": pairs / (ms * 1e-3), "ms_per_step": ms,
                      "sds_changed": int((xi != g.xi).sum())}
+    return out
+
+
+def measure_condensation(sdm, torch, g, steps=100):
+    """The condensation step on the grid (4.19M SDs, a supersaturation field
+    of +-2% over the cells), one call per step with L2 flushed between
+    steps, without and with the per-cell condensed-water output.
+    Algorithmic bytes: xi and v read (16 B) and v written (8 B) per SD."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush_r = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(5)
+    G = np.full(g.n_cells, 1.1e-10)
+    s = rng.uniform(-0.02, 0.02, g.n_cells)
+    out_d = torch.empty(g.n_cells, dtype=torch.float64, device=dev)
+    run = sdm.Run(sdm.make_config("geometric", dv=g.dv, n_cells=g.n_cells, seed=g.seed), g.n_sd)
+    run.set_attributes(g.xi, g.v, g.cell)
+    peak = measured_peaks()[0]
+    out = {"workload": "grid_geometric 4,194,304 SDs, G = 1.1e-10 m^2/s, s uniform in [-0.02, 0.02] per cell "
+                       "(rng 5), dt = 1 s, r_min = 1 um; one call per step, L2 flushed between steps",
+           "steps": steps, "algorithmic_bytes_per_sd": 24}
+    for name, want in (("update_only", False), ("with_condensed", True)):
+        for _ in range(3):
+            sdm.sdm_condensation_step(run.h, G, s, 1e-6, out=out_d if want else None, want_condensed=False,
+                                      n_cells=g.n_cells)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            torch.sum(flush_r, dim=0, out=sink)
+            a.record()
+            sdm.sdm_condensation_step(run.h, G, s, 1e-6, out=out_d if want else None, want_condensed=False,
+                                      n_cells=g.n_cells)
+            b.record()
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        gbs = 24.0 * g.n_sd / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_step": ms, "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                     "sd_updates_per_s": g.n_sd / (ms * 1e-3)}
+    run.close()
     return out
 
 

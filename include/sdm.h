@@ -84,7 +84,11 @@ typedef struct sdm_config {
      * k2 = 8e3 s^-1, k3 = 201 m^0.5 s^-1, r1 = 40e-6 m, r2 = 600e-6 m. */
     double ry_k1, ry_k2, ry_k3, ry_r1, ry_r2;
     int32_t n_cells;   /* cells of this run, >= 1 */
-    int32_t reserved0; /* must be 0 */
+    int32_t cell_base; /* index of this run's cell 0 in a larger grid split into pieces (one
+                          per context): the random streams use cell_base + c for cell c, and
+                          sedimentation counts levels from level cell_base / nx (the pieces of
+                          one grid then step exactly as the whole grid would).  0 for a whole
+                          grid; cell_base + n_cells < 2^31 */
     uint64_t seed;     /* Philox4x32-10 key of this run's random streams */
     int64_t step0;     /* index of the first step (resume: steps already done) */
     sdm_alloc_fn alloc;
@@ -208,6 +212,13 @@ const char *sdm_batch_last_error(const sdm_batch *batch);
  * [iz dz, (iz + 1) dz) above the domain bottom.  Each SD's position is kept
  * as its height zeta above its cell's bottom (binary64).
  *
+ * A context with cell_base > 0 is a piece of a larger grid: its levels are
+ * levels cell_base / nx and up of that grid (nx must divide cell_base), z
+ * is measured from the grid's bottom, and an SD falling below the piece's
+ * lowest level continues into the grid's levels below: it leaves this
+ * context (sdm_get_heights gives its new cell and height) unless it falls
+ * through the grid's bottom (precipitated).
+ *
  * One sedimentation step, for every live SD: d = v_t(r) dt in binary32 (the
  * Rogers-Yau speed of the binary32 radius of the binary32 image of the
  * volume, the twin used by SDM_PREC_KFP32, times (float)dt), widened exactly
@@ -233,6 +244,24 @@ sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double d
  * context must be created again afterwards: its next step fails with
  * SDM_ESTATE.  Errors: SDM_ESTATE (no positions), SDM_ENOMEM, SDM_ECUDA. */
 sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated);
+
+/* The same as sdm_set_positions, with zeta[n_sd] (SD-id order, host or
+ * device) the height of each SD above its cell's bottom, in [0, dz), taken
+ * as it is (no subtraction, so heights read by sdm_get_heights come back bit
+ * for bit: this is how a piece of a grid receives SDs from the piece above).
+ * Errors as sdm_set_positions. */
+sdm_status sdm_set_heights(sdm_ctx *ctx, const double *zeta, int32_t nx, double dz, int on_device);
+
+/* Heights and cells for a grid split into pieces (one context per piece of
+ * whole levels, sdm_config.cell_base its first cell): per SD in SD-id order,
+ * cell[n_sd] (nullable) its cell in the whole grid, cell_base + c, for SDs
+ * inside this piece; for an SD that left this piece through its bottom into
+ * a level of the grid below it in the last sedimentation step, its new cell
+ * there (cell < cell_base); else -1 (fallen through the grid's bottom, dead
+ * or outside).  zeta[n_sd] (nullable) the SD's height above the bottom of
+ * that cell (0 for -1).  Needs positions.  Host arrays: synchronises;
+ * device arrays: stream-ordered.  Errors: SDM_ESTATE, SDM_ENOMEM, SDM_ECUDA. */
+sdm_status sdm_get_heights(sdm_ctx *ctx, double *zeta, int32_t *cell, int on_device);
 
 /* Positions in SD-id order: z[n_sd] (nullable; needs positions) the height
  * above the domain bottom, (c / nx) dz + zeta in binary64, 0 for SDs outside

@@ -40,7 +40,7 @@ struct InstDev {
 
 struct __align__(16) WorkItem {
     int32_t inst; // index into the batch's table of InstDev pointers
-    int32_t cell; // cell within that run
+    int32_t cell; // the cell's index in the random streams (its run's cell_base + cell)
     int32_t off;  // the cell's first storage slot (the plan is rebuilt when the layout changes)
     int32_t n;    // the cell's storage slots
 };

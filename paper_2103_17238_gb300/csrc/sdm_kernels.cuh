@@ -942,7 +942,7 @@ struct BigCell {
     int32_t n;        // stored SDs of the cell
     int32_t lb;       // log2 of top-level buckets
     int32_t n_chunks;
-    int32_t pad_;
+    int32_t rcell;    // the cell's index in the random streams (its run's cell_base + cell)
     int64_t hist_base; // into the per-(chunk, bucket) count array
     int64_t sd_base;   // into the key / rank / perm scratch
     int64_t bkt_base;  // into the bucket-start array (2^lb + 1 entries)
@@ -988,7 +988,7 @@ __device__ __forceinline__ void big_chunk_keys(const InstDev *P, const BigCell &
     for (int i = 0; i < QPT; ++i) {
         const int q = lo2 + (int)threadIdx.x + i * kBigNT;
         if ((x[i].x > 0) | (x[i].y > 0)) {
-            const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)bc.cell, s, 0u);
+            const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)bc.rcell, s, 0u);
             if (x[i].x > 0)
                 f(((uint64_t)w.x << 32) | w.y, (uint32_t)(2 * q));
             if (x[i].y > 0)
@@ -1142,7 +1142,7 @@ __global__ void __launch_bounds__(kBucketNT) big_bucket_sort_kernel(const BigBuc
     const InstDev *P = insts[bc.inst];
     const uint64_t seed = P->seed;
     const int64_t s = P->step + step_offset;
-    const uint32_t cell = (uint32_t)bc.cell;
+    const uint32_t cell = (uint32_t)bc.rcell;
     if (nb > (uint32_t)kBucketCap) {
         // overfull bucket (never expected for uniform keys): rank by counting
         for (uint32_t e = threadIdx.x; e < nb; e += kBucketNT) {
@@ -1216,7 +1216,7 @@ __global__ void __launch_bounds__(kPairNT) big_pairs_kernel(const BigPairs *__re
     double *__restrict__ gv = P->v + off;
     const uint32_t *perm = S.perm + bc.sd_base;
     const float ratio_f = u32_to_f32_rn((n_c & 1u) ? n_c : n_c - 1u);
-    const uint4 w = draw4(P->seed, q, (uint32_t)bc.cell, s, 1u);
+    const uint4 w = draw4(P->seed, q, (uint32_t)bc.rcell, s, 1u);
     // both pairs' SDs are gathered at once (eight independent loads)
     uint32_t A[2], B[2];
     int64_t XA[2], XB[2];

@@ -120,8 +120,10 @@ extern "C" sdm_status sdm_cell_step_noalloc(const sdm_config *cfg, int64_t step,
     sdm_status st = check_config(cfg, nullptr);
     if (st != SDM_OK)
         return st;
-    if (cfg->n_cells != 1)
-        return fail(nullptr, SDM_EINVAL, "sdm_cell_step_noalloc: cfg->n_cells must be 1 (one cell per call)");
+    if (cfg->n_cells != 1 || cfg->cell_base != 0)
+        return fail(nullptr, SDM_EINVAL,
+                    "sdm_cell_step_noalloc: cfg->n_cells must be 1 and cfg->cell_base 0 (one cell per call, random "
+                    "streams of cell index 0)");
     if (step < 0)
         return fail(nullptr, SDM_EINVAL, "sdm_cell_step_noalloc: step must be >= 0");
     if (n_sd < 2 || n_sd > kNaMaxSd || (n_sd & 1))

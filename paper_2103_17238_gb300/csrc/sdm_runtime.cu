@@ -540,12 +540,13 @@ sdm_status build_plan(sdm_batch *b)
                 continue;
             const int cls = class_of(n, tun);
             if (cls >= 0) {
-                items[cls].push_back(WorkItem{i, cell, c->h_cell_off[cell], n});
+                items[cls].push_back(WorkItem{i, c->cfg.cell_base + cell, c->h_cell_off[cell], n});
                 continue;
             }
             BigCell bc{};
             bc.inst = i;
             bc.cell = cell;
+            bc.rcell = c->cfg.cell_base + cell;
             bc.n = n;
             bc.lb = big_lb(n);
             bc.n_chunks = (n + kBigChunk - 1) / kBigChunk;
@@ -844,8 +845,8 @@ sdm_status check_config(const sdm_config *cfg, std::string *err)
         return fail(err, SDM_EINVAL, "Rogers-Yau coefficients must be finite, > 0, r1 < r2");
     if (cfg->n_cells < 1)
         return fail(err, SDM_EINVAL, "n_cells must be >= 1");
-    if (cfg->reserved0 != 0)
-        return fail(err, SDM_EINVAL, "reserved0 must be 0");
+    if (cfg->cell_base < 0 || (int64_t)cfg->cell_base + cfg->n_cells > INT32_MAX)
+        return fail(err, SDM_EINVAL, "cell_base = %d: cell_base + n_cells must lie in [0, 2^31)", cfg->cell_base);
     if (cfg->step0 < 0)
         return fail(err, SDM_EINVAL, "step0 must be >= 0");
     if ((cfg->alloc == nullptr) != (cfg->free == nullptr))

@@ -35,12 +35,14 @@ constexpr int kRadixTile = kRadixNT * kRadixRounds; // keys per block and pass
 constexpr int kRadixBuckets = 256;                  // 8-bit digits
 
 // ------------------------------------------------------------------ kernels
-// zeta of every slot from z (SD-id order): z - (c / nx) dz, which must lie
-// in [0, dz); flags bit 0 and the first bad id on failure.  SDs outside the
+// zeta of every slot from z (SD-id order): z - (level) dz with level =
+// (cbase + c) / nx, which must lie in [0, dz) (zeta_in: z already holds
+// zeta); flags bit 0 and the first bad id on failure.  SDs outside the
 // domain and padding slots get zeta 0.  group[slot] = the slot's group.
 __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restrict__ cell_off, int32_t n_cells,
                                                          int64_t n_slots, const int32_t *__restrict__ id_of_slot,
                                                          const double *__restrict__ z, int32_t nx, double dz,
+                                                         int32_t cbase, int zeta_in,
                                                          double *__restrict__ zeta, int32_t *__restrict__ group,
                                                          uint32_t *__restrict__ flags,
                                                          unsigned long long *__restrict__ bad)
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restri
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int g = gw; g <= n_cells; g += nw) {
         const int64_t lo = cell_off[g], hi = g < n_cells ? cell_off[g + 1] : n_slots;
-        const double base = __dmul_rn((double)(g / nx), dz);
+        const double base = zeta_in ? 0.0 : __dmul_rn((double)((g + cbase) / nx), dz);
         for (int64_t s = lo + lane; s < hi; s += 32) {
             const int32_t id = id_of_slot[s];
             double zt = 0.0;
@@ -68,17 +70,23 @@ __global__ void __launch_bounds__(kSedNT) sed_set_kernel(const int32_t *__restri
     }
 }
 
-// z[id] = (c / nx) dz + zeta (0 outside) and cell[id] = c (-1 outside).
+// z[id] = ((cbase + c) / nx) dz + zeta (0 outside) and cell[id] = c (-1
+// outside).  zeta_out[id] = zeta of the slot, and gcell[id] = cbase + c
+// inside, else emig[id]: the cell of another piece of the grid that the SD
+// entered through this piece's bottom in the last sedimentation step, or -1
+// (zeta_out then its height in that cell, else 0).
 __global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restrict__ cell_off, int32_t n_cells,
                                                          int64_t n_slots, const int32_t *__restrict__ id_of_slot,
                                                          const double *__restrict__ zeta, int32_t nx, double dz,
-                                                         double *__restrict__ z, int32_t *__restrict__ cell)
+                                                         int32_t cbase, const int32_t *__restrict__ emig,
+                                                         double *__restrict__ z, int32_t *__restrict__ cell,
+                                                         double *__restrict__ zeta_out, int32_t *__restrict__ gcell)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int g = gw; g <= n_cells; g += nw) {
         const int64_t lo = cell_off[g], hi = g < n_cells ? cell_off[g + 1] : n_slots;
-        const double base = g < n_cells && z ? __dmul_rn((double)(g / nx), dz) : 0.0;
+        const double base = g < n_cells && z ? __dmul_rn((double)((g + cbase) / nx), dz) : 0.0;
         for (int64_t s = lo + lane; s < hi; s += 32) {
             const int32_t id = id_of_slot[s];
             if (id < 0)
@@ -87,6 +95,10 @@ __global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restri
                 z[id] = g < n_cells ? __dadd_rn(base, zeta[s]) : 0.0;
             if (cell)
                 cell[id] = g < n_cells ? g : -1;
+            if (zeta_out)
+                zeta_out[id] = zeta[s];
+            if (gcell)
+                gcell[id] = g < n_cells ? g + cbase : (emig ? emig[id] : -1);
         }
     }
 }
@@ -96,7 +108,11 @@ __global__ void __launch_bounds__(kSedNT) sed_get_kernel(const int32_t *__restri
 // = its slot, zeta_new[slot] = its new height; counts[new group] (one
 // atomic per run of equal groups among a warp's 32 consecutive slots);
 // precip_part[block] = sum of xi v of the SDs that fell through the bottom
-// (thread order fixed, then a fixed tree over the block).
+// of the grid (thread order fixed, then a fixed tree over the block).
+// Levels are counted from the grid's bottom (cell cbase + c): an SD that
+// leaves this piece's lowest level into a level of another piece becomes
+// outside here, with emig[id] = its new cell there and zeta_new its height
+// in it (emig[id] = -1 for every other SD).
 constexpr int kSedU = 4;
 constexpr int kSedMaxBlocks = 4096;
 
@@ -129,7 +145,8 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
                                                           const int32_t *__restrict__ id_of_slot,
                                                           uint32_t *__restrict__ key, uint32_t *__restrict__ val,
                                                           double *__restrict__ zeta_new, uint32_t *__restrict__ counts,
-                                                          double *__restrict__ precip_part)
+                                                          double *__restrict__ precip_part, int32_t cbase,
+                                                          int32_t *__restrict__ emig)
 {
     constexpr unsigned FULL = 0xFFFFFFFFu;
     __shared__ double s_pr[kSedNT / 32];
@@ -160,35 +177,41 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
             int32_t ng = -1; // -1: no SD in this slot
             if (id[u] >= 0) {
                 double zn = 0.0;
+                int32_t em = -1;
                 ng = n_cells;
                 if (g[u] < n_cells && x[u] > 0) {
                     bool in_range;
                     const float vf = d2f_rn(vv[u], in_range);
                     const double d = f2d_exact(__fmul_rn(vt32c(C, radius32(vf)), dt32));
                     double zz = __dsub_rn(zt[u], d);
-                    // crossing k levels takes cell c to c - k nx; below level 0
-                    // exactly when that is negative (0 <= column < nx)
+                    // crossing k levels takes cell c to c - k nx; below the
+                    // grid's level 0 exactly when cbase + c is negative
+                    // (0 <= column < nx)
                     int32_t c = g[u];
                     while (dneg(zz)) { // at most as many levels as the SD falls through
                         c -= nx;
-                        if (c < 0)
+                        if (c + cbase < 0)
                             break;
                         zz = __dadd_rn(zz, dz);
                     }
-                    if (c < 0) {
+                    if (c + cbase < 0) {
                         pr = __dadd_rn(pr, __dmul_rn(xi2d(x[u]), vv[u]));
                     } else {
                         if (dge_pos(zz, dz)) { // zeta + dz rounded up to dz: on the boundary, level above
                             c += nx;
                             zz = 0.0;
                         }
-                        ng = c;
                         zn = zz;
+                        if (c >= 0)
+                            ng = c;
+                        else // into another piece of the grid
+                            em = c + cbase;
                     }
                 }
                 key[id[u]] = (uint32_t)ng;
                 val[id[u]] = (uint32_t)sl;
                 zeta_new[sl] = zn;
+                emig[id[u]] = em;
             }
             const int32_t nxt = __shfl_down_sync(FULL, ng, 1);
             const bool end = lane == 31 || nxt != ng;
@@ -431,6 +454,7 @@ struct SedBuffers {
     double *precip = nullptr;   // per-block parts of the move kernel, then the total
     uint32_t *hist = nullptr;   // 256 x tiles, then 256 digit totals
     uint32_t *flags = nullptr;  // flags, then the first bad id (8-byte aligned)
+    int32_t *emig = nullptr;    // per SD id: its cell in another piece of the grid after the last step, or -1
 };
 
 void sed_release(sdm_ctx *ctx)
@@ -439,7 +463,7 @@ void sed_release(sdm_ctx *ctx)
         SedBuffers &b = *ctx->sed;
         void *bufs[] = {b.xi2,      b.v2,       b.zeta2,    b.id2,    b.group,  b.group2,
                         b.cell_off2, b.zeta_new, b.keys[0], b.keys[1], b.vals[0], b.vals[1],
-                        b.counts,   b.ustart,   b.precip,   b.hist,   b.flags};
+                        b.counts,   b.ustart,   b.precip,   b.hist,   b.flags,  b.emig};
         for (void *p : bufs)
             ctx->mem.put(p, 0);
         delete ctx->sed;
@@ -484,14 +508,15 @@ sdm_status sed_alloc(sdm_ctx *ctx)
     b.precip = sed_get<double>(ctx, (size_t)kSedMaxBlocks + 1);
     b.hist = sed_get<uint32_t>(ctx, (size_t)kRadixBuckets * tiles + kRadixBuckets);
     b.flags = sed_get<uint32_t>(ctx, 4);
+    b.emig = sed_get<int32_t>(ctx, cap);
     const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.group && b.group2 && b.cell_off2 &&
-                    b.zeta_new && b.keys[0] &&
-                    b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart && b.precip && b.hist && b.flags;
+                    b.zeta_new && b.keys[0] && b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart &&
+                    b.precip && b.hist && b.flags && b.emig;
     if (!ok) {
         sed_release(ctx);
         return fail(&ctx->error, SDM_ENOMEM, "sedimentation buffers: device allocation failed");
     }
-    ctx->device_bytes += slots * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 8) + cap * 16 + ((int64_t)nc + 2) * 16 +
+    ctx->device_bytes += slots * (8 + 8 + 8 + 8 + 4 + 4 + 4 + 8) + cap * 20 + ((int64_t)nc + 2) * 16 +
                          (int64_t)kRadixBuckets * (tiles + 1) * 4;
     return SDM_OK;
 }
@@ -503,9 +528,12 @@ int sed_grid(int32_t n_groups)
 
 } // namespace
 
-extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device)
+namespace {
+
+// sdm_set_positions (zeta_in = 0: z above the grid's bottom) and
+// sdm_set_heights (zeta_in = 1: z holds the heights above the cells' bottoms)
+sdm_status set_positions_impl(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device, int zeta_in)
 {
-    NvtxRange nvtx_range("sdm_set_positions");
     sdm_status st = ctx_usable(ctx);
     if (st != SDM_OK)
         return st;
@@ -514,6 +542,9 @@ extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t n
     const int32_t nc = ctx->cfg.n_cells;
     if (!z || nx < 1 || nc % nx != 0 || !(std::isfinite(dz) && dz > 0.0))
         return fail(&ctx->error, SDM_EINVAL, "need z, nx >= 1 dividing n_cells = %d, and a finite dz > 0", nc);
+    if (ctx->cfg.cell_base % nx != 0)
+        return fail(&ctx->error, SDM_EINVAL, "nx = %d must divide cell_base = %d (pieces of a grid are whole levels)",
+                    nx, ctx->cfg.cell_base);
     st = sed_alloc(ctx);
     if (st != SDM_OK)
         return st;
@@ -533,7 +564,9 @@ extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t n
     CTX_CUDA(ctx, cudaMemsetAsync(d_flags, 0, sizeof(uint32_t), s));
     CTX_CUDA(ctx, cudaMemsetAsync(d_bad, 0xFF, sizeof(unsigned long long), s));
     sed_set_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot, dz_arr,
-                                                        nx, dz, ctx->d_zeta, ctx->sed->group, d_flags, d_bad);
+                                                        nx, dz, ctx->cfg.cell_base, zeta_in, ctx->d_zeta,
+                                                        ctx->sed->group, d_flags, d_bad);
+    CTX_CUDA(ctx, cudaMemsetAsync(ctx->sed->emig, 0xFF, sizeof(int32_t) * ctx->n_sd, s));
     uint32_t flags = 0;
     unsigned long long bad = 0;
     CTX_CUDA(ctx, cudaGetLastError());
@@ -543,12 +576,28 @@ extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t n
     ctx->mem.put(stage, bz);
     if (flags & 1u) {
         ctx->has_positions = false;
-        return fail(&ctx->error, SDM_EINVAL, "SD %llu: z must lie in its cell's level [iz dz, (iz + 1) dz)", bad);
+        return fail(&ctx->error, SDM_EINVAL,
+                    zeta_in ? "SD %llu: zeta must lie in [0, dz)" : "SD %llu: z must lie in its cell's level [iz dz, (iz + 1) dz)",
+                    bad);
     }
     ctx->nx = nx;
     ctx->dz = dz;
     ctx->has_positions = true;
     return SDM_OK;
+}
+
+} // namespace
+
+extern "C" sdm_status sdm_set_positions(sdm_ctx *ctx, const double *z, int32_t nx, double dz, int on_device)
+{
+    NvtxRange nvtx_range("sdm_set_positions");
+    return set_positions_impl(ctx, z, nx, dz, on_device, 0);
+}
+
+extern "C" sdm_status sdm_set_heights(sdm_ctx *ctx, const double *zeta, int32_t nx, double dz, int on_device)
+{
+    NvtxRange nvtx_range("sdm_set_heights");
+    return set_positions_impl(ctx, zeta, nx, dz, on_device, 1);
 }
 
 extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
@@ -568,7 +617,7 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
         1, std::min<int64_t>(kSedMaxBlocks, (ctx->n_slots + (int64_t)kSedNT * kSedU - 1) / ((int64_t)kSedNT * kSedU)));
     sed_move_kernel<<<move_blocks, kSedNT, 0, s>>>(ctx->d_inst, nc, ctx->n_slots, ctx->nx, ctx->dz, (float)ctx->cfg.dt,
                                                    ctx->d_zeta, b.group, ctx->d_id_of_slot, b.keys[0], b.vals[0],
-                                                   b.zeta_new, b.counts, b.precip);
+                                                   b.zeta_new, b.counts, b.precip, ctx->cfg.cell_base, b.emig);
     sed_scan_kernel<<<1, 1024, 0, s>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, move_blocks,
                                        b.precip + kSedMaxBlocks);
     // stable sort of the new groups, SD-id order in
@@ -645,7 +694,8 @@ extern "C" sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, 
     const int64_t n = ctx->n_sd;
     if (on_device) {
         sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
-                                                            ctx->d_zeta, nx, ctx->dz, z, cell);
+                                                            ctx->d_zeta, nx, ctx->dz, ctx->cfg.cell_base, nullptr, z,
+                                                            cell, nullptr, nullptr);
         CTX_CUDA(ctx, cudaGetLastError());
         return SDM_OK;
     }
@@ -654,11 +704,51 @@ extern "C" sdm_status sdm_get_positions(sdm_ctx *ctx, double *z, int32_t *cell, 
     if (!tmp)
         return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
     sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
-                                                        ctx->d_zeta, nx, ctx->dz, z ? (double *)tmp : nullptr,
-                                                        cell ? (int32_t *)(tmp + bz) : nullptr);
+                                                        ctx->d_zeta, nx, ctx->dz, ctx->cfg.cell_base, nullptr,
+                                                        z ? (double *)tmp : nullptr,
+                                                        cell ? (int32_t *)(tmp + bz) : nullptr, nullptr, nullptr);
     CTX_CUDA(ctx, cudaGetLastError());
     if (z)
         CTX_CUDA(ctx, cudaMemcpyAsync(z, tmp, bz, cudaMemcpyDeviceToHost, s));
+    if (cell)
+        CTX_CUDA(ctx, cudaMemcpyAsync(cell, tmp + bz, bc, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->mem.put(tmp, bz + bc);
+    return check_device_status(ctx);
+}
+
+extern "C" sdm_status sdm_get_heights(sdm_ctx *ctx, double *zeta, int32_t *cell, int on_device)
+{
+    NvtxRange nvtx_range("sdm_get_heights");
+    sdm_status st = ctx_usable(ctx);
+    if (st != SDM_OK)
+        return st;
+    if (!ctx->has_attributes || !ctx->has_positions)
+        return fail(&ctx->error, SDM_ESTATE, "no positions: sdm_set_positions has not been called");
+    if (!zeta && !cell)
+        return SDM_OK;
+    cudaStream_t s = ctx->stream;
+    const int32_t nc = ctx->cfg.n_cells;
+    const int64_t n = ctx->n_sd;
+    const int32_t *emig = ctx->sed->emig;
+    if (on_device) {
+        sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
+                                                            ctx->d_zeta, ctx->nx, ctx->dz, ctx->cfg.cell_base, emig,
+                                                            nullptr, nullptr, zeta, cell);
+        CTX_CUDA(ctx, cudaGetLastError());
+        return SDM_OK;
+    }
+    const size_t bz = sizeof(double) * n, bc = sizeof(int32_t) * n;
+    char *tmp = (char *)ctx->mem.get(bz + bc);
+    if (!tmp)
+        return fail(&ctx->error, SDM_ENOMEM, "allocation failed");
+    sed_get_kernel<<<sed_grid(nc + 1), kSedNT, 0, s>>>(ctx->d_cell_off, nc, ctx->n_slots, ctx->d_id_of_slot,
+                                                        ctx->d_zeta, ctx->nx, ctx->dz, ctx->cfg.cell_base, emig, nullptr,
+                                                        nullptr, zeta ? (double *)tmp : nullptr,
+                                                        cell ? (int32_t *)(tmp + bz) : nullptr);
+    CTX_CUDA(ctx, cudaGetLastError());
+    if (zeta)
+        CTX_CUDA(ctx, cudaMemcpyAsync(zeta, tmp, bz, cudaMemcpyDeviceToHost, s));
     if (cell)
         CTX_CUDA(ctx, cudaMemcpyAsync(cell, tmp + bz, bc, cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));

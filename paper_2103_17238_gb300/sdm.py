@@ -31,6 +31,7 @@ EXPORTS = [
     "sdm_batch_create", "sdm_batch_step", "sdm_batch_destroy", "sdm_batch_last_error",
     "sdm_cell_step_noalloc", "sdm_set_tuning", "sdm_get_tuning",
     "sdm_set_positions", "sdm_sedimentation_step", "sdm_get_positions", "sdm_condensation_step",
+    "sdm_set_heights", "sdm_get_heights",
     "sdm_diagnostics", "sdm_selftest_bounded_wait",
 ]
 NOALLOC_MAX_SD = 1 << 20
@@ -59,7 +60,7 @@ class sdm_config(ctypes.Structure):
         ("ry_r1", ctypes.c_double),
         ("ry_r2", ctypes.c_double),
         ("n_cells", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("cell_base", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("step0", ctypes.c_int64),
         ("alloc", ALLOC_FN),
@@ -140,6 +141,8 @@ def load(path: str = LIB_PATH):
         L.sdm_sedimentation_step.argtypes = [vp, P(ctypes.c_double)]
         L.sdm_condensation_step.argtypes = [vp, vp, vp, ctypes.c_double, vp, ctypes.c_int]
         L.sdm_get_positions.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.sdm_set_heights.argtypes = [vp, vp, i32, ctypes.c_double, ctypes.c_int]
+        L.sdm_get_heights.argtypes = [vp, vp, vp, ctypes.c_int]
         L.sdm_get_tuning.argtypes = [P(sdm_tuning)]
         L.sdm_diagnostics.argtypes = [vp, P(sdm_diag)]
         L.sdm_selftest_bounded_wait.argtypes = [vp, i64]
@@ -395,6 +398,21 @@ def sdm_get_positions(ctx, n_sd: int | None = None, z=None, cell=None, want_z: b
     return z, cell
 
 
+def sdm_set_heights(ctx, zeta, nx: int, dz: float):
+    pz, dev, kz = _ptr_and_flag(zeta, np.float64)
+    _check(load().sdm_set_heights(ctx, pz, int(nx), float(dz), dev), "sdm_set_heights", ctx)
+
+
+def sdm_get_heights(ctx, n_sd: int | None = None):
+    """(zeta, cell) in SD-id order: heights above the cells' bottoms and the
+    cells in the whole grid (see include/sdm.h), numpy."""
+    n = int(n_sd if n_sd is not None else sdm_get_info(ctx).n_sd)
+    zz = np.zeros(n, dtype=np.float64)
+    cc = np.zeros(n, dtype=np.int32)
+    _check(load().sdm_get_heights(ctx, zz.ctypes.data, cc.ctypes.data, 0), "sdm_get_heights", ctx)
+    return zz, cc
+
+
 def sdm_set_tuning(tuning=None):
     """tuning: dict with smem_max_sd, warp_cell_max, warps_per_block and
     optionally fuse_steps (absent: the default, FUSE_STEPS_DEFAULT steps per
@@ -416,7 +434,7 @@ def sdm_get_tuning() -> dict:
 
 # ------------------------------------------------------------ owners
 def make_config(kernel="golovin", precision="fp64", *, b=1500.0, dt=1.0, dv=1.0e6, n_cells=1, seed=0,
-                step0=0, **ry) -> sdm_config:
+                step0=0, cell_base=0, **ry) -> sdm_config:
     cfg = sdm_config_default()
     cfg.kernel = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -426,6 +444,7 @@ def make_config(kernel="golovin", precision="fp64", *, b=1500.0, dt=1.0, dv=1.0e
     cfg.n_cells = n_cells
     cfg.seed = seed
     cfg.step0 = step0
+    cfg.cell_base = cell_base
     for k, v in ry.items():
         setattr(cfg, "ry_" + k, v)
     return cfg
