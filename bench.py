@@ -77,18 +77,40 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+def profiled(key: str):
+    """A per-launch figure (e.g. traffic_bytes_per_launch) from the committed
+    ncu summary, if it was taken on the current kernel sources."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m = re.search(key + r":\s*([0-9.eE+]+)", txt)
     hsh = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or not hsh or hsh.group(1) != kernel_source_hash():
         return None
     return float(m.group(1))
+
+
+def profiled_traffic():
+    return profiled("traffic_bytes_per_launch")
+
+
+SMS, SCHEDULERS_PER_SM = 152, 4
+
+
+def issue_roofline(avg_kernel_s: float, sm_mhz):
+    """The step kernel against the SMs' instruction issue rate: warp
+    instructions per launch (ncu, the captured launch) over one instruction
+    per scheduler per cycle on all SMs at the sampled SM clock."""
+    inst = profiled("warp_instructions_per_launch")
+    if inst is None or not sm_mhz:
+        return None
+    peak = SMS * SCHEDULERS_PER_SM * sm_mhz * 1e6  # warp instructions / s
+    achieved = inst / avg_kernel_s
+    return {"bound": "issue", "achieved": round(achieved / 1e9, 1), "peak": round(peak / 1e9, 1),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "warp_instructions_per_launch": inst, "floor_us": round(inst / peak * 1e6, 2),
+            "note": "instructions of the captured launch (the first timed step); later steps of a run issue more"}
 
 
 def measured_peaks():
@@ -269,6 +291,7 @@ def run_ours(args, rank: int, world: int):
                 "algorithmic_bytes_per_launch": int(alg_bytes),
                 "frac_of_nominal_8TBps": round(achieved / 8000.0, 4)}
 
+    roofline["issue"] = issue_roofline(avg_kernel_s, clocks.get("sm_mhz") if isinstance(clocks, dict) else None)
     e2e = measure_e2e(args, g, sdm, torch, pairs0)
     run.close()
     extras = {}
@@ -675,6 +698,14 @@ def measure_serving(torch, n_requests=200):
     res = serve.Server(budget_bytes=120 * 10**9, chunk=20, fuse_steps=20).serve(reqs)
     out["fused_ticks"] = {"pair_updates_per_s": res["pair_updates_per_s"], "step_latency_ms": res["step_latency_ms"],
                           "time_in_system_s": res["time_in_system_s"], "max_active": res["max_active"]}
+    # capacity: the same requests arriving all at once (arrival times / 1e6),
+    # so that the device, not the arrival process, sets the rate
+    for name, fuse in (("saturated", 0), ("saturated_fused_ticks", 20)):
+        res = serve.Server(budget_bytes=120 * 10**9, chunk=20, fuse_steps=fuse, time_scale=1e6).serve(reqs)
+        out[name] = {"requests_per_s": res["requests_per_s"], "pair_updates_per_s": res["pair_updates_per_s"],
+                     "pair_updates_per_device_s": res["pair_updates_per_device_s"],
+                     "step_latency_ms": res["step_latency_ms"], "time_in_system_s": res["time_in_system_s"],
+                     "max_active": res["max_active"], "wall_s": res["wall_s"], "device_busy_s": res["device_busy_s"]}
     return out
 
 

@@ -51,15 +51,19 @@ struct CondBuffers {
     double *cond = nullptr;        // n_cells
     float *h_cf = nullptr;         // page-locked staging of cf
     cudaEvent_t cf_done = nullptr; // the last copy out of h_cf
+    std::vector<float> last_cf;    // cf on the device (no copy when a call repeats it)
 };
 
 // f2d_exact (sdm_sediment.cu): the exact widening of a binary32 on the
 // integer pipe.
 
-// dV of one live SD (the reading above), binary32
+// dV of one live SD (the reading above), binary32.  The binary32 image of
+// v is rounded on the integer pipe (d2f_rn): the conversion instruction would
+// take the narrow binary64 pipe, which then bounds the kernel.
 __device__ __forceinline__ float condense_dv(double v, float cf, float xminf)
 {
-    const float r = radius32(__double2float_rn(v));
+    bool in_range;
+    const float r = radius32(d2f_rn(v, in_range)); // volumes lie in [1e-30, 1e30]: always in range
     const float x = __fmul_rn(r, r);
     float xn = __fadd_rn(x, cf);
     const float lo = x < xminf ? x : xminf;
@@ -262,11 +266,16 @@ extern "C" sdm_status sdm_condensation_step(sdm_ctx *ctx, const double *G, const
         return st;
     CondBuffers &b = *ctx->cond;
     cudaStream_t cs = ctx->stream;
-    CTX_CUDA(ctx, cudaEventSynchronize(b.cf_done)); // the staging's last copy has left
+    std::vector<float> cf(nc);
     for (int32_t c = 0; c < nc; ++c)
-        b.h_cf[c] = (float)(((2.0 * G[c]) * s[c]) * dt);
-    CTX_CUDA(ctx, cudaMemcpyAsync(b.cf, b.h_cf, sizeof(float) * nc, cudaMemcpyHostToDevice, cs));
-    CTX_CUDA(ctx, cudaEventRecord(b.cf_done, cs));
+        cf[c] = (float)(((2.0 * G[c]) * s[c]) * dt);
+    if (cf != b.last_cf) { // a new field (a repeated one is on the device already)
+        CTX_CUDA(ctx, cudaEventSynchronize(b.cf_done)); // the staging's last copy has left
+        std::memcpy(b.h_cf, cf.data(), sizeof(float) * nc);
+        CTX_CUDA(ctx, cudaMemcpyAsync(b.cf, b.h_cf, sizeof(float) * nc, cudaMemcpyHostToDevice, cs));
+        CTX_CUDA(ctx, cudaEventRecord(b.cf_done, cs));
+        b.last_cf.swap(cf);
+    }
     const float xminf = (float)(r_min * r_min);
     if (b.n_items > 0) {
         const int grid = (int)std::min<int64_t>((b.n_items + kCondNT / 32 - 1) / (kCondNT / 32), 152 * 8);

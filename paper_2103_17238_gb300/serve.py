@@ -13,8 +13,9 @@ dv/dlnr spectrum and final state and leave; their memory admits the next
 ones.  Every run keeps its own seed and step counter, so its result is the
 same alone and in any mix.
 
-Metrics: per-run step latency (tick wall time / steps of the tick, each run
-in the tick), time in system, and aggregate pair-updates/s.
+Metrics: per-run step latency (tick time on the device / steps of the tick,
+each run in the tick), time in system, requests/s and aggregate
+pair-updates/s over the wall time (and over the device's busy time).
 """
 from __future__ import annotations
 
@@ -76,6 +77,12 @@ class Server:
             sdm.sdm_set_tuning(prev)
 
     def serve(self, requests: list[I.Request]) -> dict:
+        """Serves the requests (their arrival times, divided by time_scale,
+        are seconds after the call).  A tick is enqueued without waiting; the
+        requests that arrive meanwhile are admitted (their state uploaded on
+        a stream of their own) while the tick runs on the device, and join
+        at the next tick.  Tick times are CUDA-event times of the batch's
+        stream."""
         import torch
 
         pending = [Served(r) for r in sorted(requests, key=lambda r: r.arrival)]
@@ -85,7 +92,10 @@ class Server:
                 raise sdm.SdmError(sdm.SDM_EBUDGET, "serve", f"request needs {s.footprint} B > budget")
             live = np.bincount(s.req.inst.cell[s.req.inst.xi > 0], minlength=s.req.inst.n_cells)
             s.pairs_per_step = int((live // 2).sum())
-        active: list[Served] = []
+        main = torch.cuda.current_stream()
+        admit_stream = torch.cuda.Stream()
+        active: list[Served] = []   # in the batch
+        joining: list[Served] = []  # admitted, in the batch from the next tick
         finished: list[Served] = []
         used = 0
         batch = None
@@ -95,36 +105,45 @@ class Server:
         max_used = 0
         t0 = time.perf_counter()
         pair_updates = 0
-        while pending or active:
+        tick_ms = []
+
+        def admit():
+            nonlocal used, max_used
             now = (time.perf_counter() - t0) * self.time_scale
-            # admit every arrived request that fits (arrival order)
-            admitted = False
             while pending and pending[0].req.arrival <= now and used + pending[0].footprint <= self.budget:
                 s = pending.pop(0)
-                s.run = make_run(s.req.inst)
+                with torch.cuda.stream(admit_stream):
+                    s.run = make_run(s.req.inst)  # returns after its upload has landed
                 s.admitted_at = time.perf_counter() - t0
                 used += s.footprint
-                active.append(s)
-                admitted = True
+                joining.append(s)
+            max_used = max(max_used, used)
+
+        while pending or active or joining:
+            admit()
+            active += joining
+            joining.clear()
             if not active:
                 # idle until the next arrival
                 wait = pending[0].req.arrival / self.time_scale - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(min(wait, 0.01))
                 continue
-            if admitted or batch is None or members != [id(s) for s in active]:
+            if batch is None or members != [id(s) for s in active]:
                 if batch is not None:
                     batch.close()
                 batch = self._batch([s.run for s in active])
                 members = [id(s) for s in active]
             max_active = max(max_active, len(active))
-            max_used = max(max_used, used)
             k = min(self.chunk, min(s.req.inst.steps - s.done for s in active))
-            torch.cuda.synchronize()
-            ts = time.perf_counter()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(main)
             batch.step(k)
-            torch.cuda.synchronize()
-            dt_ms = (time.perf_counter() - ts) * 1e3
+            e1.record(main)
+            admit()  # overlaps the tick on the device
+            e1.synchronize()
+            dt_ms = e0.elapsed_time(e1)
+            tick_ms.append(dt_ms)
             ticks += 1
             for s in active:
                 s.done += k
@@ -154,6 +173,7 @@ class Server:
         wall = time.perf_counter() - t0
         lat = np.concatenate([np.asarray(s.step_latency_ms) for s in finished]) if finished else np.zeros(0)
         tis = np.array([s.finished_at - s.req.arrival / self.time_scale for s in finished])
+        busy = sum(tick_ms) / 1e3
         return {
             "served": finished,
             "requests": len(finished),
@@ -161,8 +181,11 @@ class Server:
             "max_active": max_active,
             "max_used_bytes": max_used,
             "wall_s": wall,
+            "device_busy_s": busy,
+            "requests_per_s": len(finished) / wall if wall > 0 else 0.0,
             "pair_updates": pair_updates,
             "pair_updates_per_s": pair_updates / wall if wall > 0 else 0.0,
+            "pair_updates_per_device_s": pair_updates / busy if busy > 0 else 0.0,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)) if lat.size else None,
                                 "p99": float(np.percentile(lat, 99)) if lat.size else None},
             "time_in_system_s": {"p50": float(np.percentile(tis, 50)) if tis.size else None,
