@@ -318,9 +318,14 @@ typedef struct sdm_tuning {
                               * launch per step, and a one-step call is one launch either way.
                               * 0 or 1: one launch per step for every cell.  A graph captures the
                               * same launches. */
+    int32_t mid_max_sd;      /* largest cell above smem_max_sd stepped by one thread-block cluster
+                              * (1, 2 or 4 CTAs of up to 16384 SDs each, the whole step in shared
+                              * and distributed shared memory); larger cells take the multi-pass
+                              * global path.  0: no cluster path.  Default SDM_MID_MAX_SD_DEFAULT. */
 } sdm_tuning;
 
 #define SDM_FUSE_STEPS_DEFAULT 64
+#define SDM_MID_MAX_SD_DEFAULT 16384
 
 /* NULL restores the defaults.  Errors: SDM_EINVAL. */
 sdm_status sdm_set_tuning(const sdm_tuning *tuning);

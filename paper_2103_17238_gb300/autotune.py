@@ -1,6 +1,7 @@
 """Autotuner of the launch shape: which cells go through the shared-memory
-sort (and which through the multi-pass global path), which cells run one
-warp per cell, and how many warps share a block.
+sort, which through the cluster path and which through the multi-pass global
+path, which cells run one warp per cell, how many warps share a block, and
+how many steps the warp-per-cell kernel fuses per launch.
 
 The tuning never changes results: every candidate computes the same state bit
 for bit.  The tuner times each candidate on the caller's own runs (one fused
@@ -27,6 +28,9 @@ CANDIDATES = [
     for w in (0, 128, 256, 512)
     for k in ((2,) if w == 0 else (1, 2, 4))
 ]
+MID_CHOICES = (0, 16384, 32768, 65536)  # largest cell on the cluster path (0: none)
+FUSE_CHOICES = (0, 8, sdm.FUSE_STEPS_DEFAULT)
+DEFAULT_SHAPE = dict(smem_max_sd=4096, warp_cell_max=512, warps_per_block=2)
 
 
 def signature(runs) -> str:
@@ -74,12 +78,25 @@ def time_candidate(runs, steps: int) -> float:
     return e0.elapsed_time(e1) / steps
 
 
+def _search(runs, steps, cands, timings):
+    out = []
+    for c in cands:
+        sdm.sdm_set_tuning(c)
+        t = time_candidate(runs, steps)
+        out.append((t, c))
+        timings.append((t, c))
+    return min(out, key=lambda x: x[0])
+
+
 def tune(runs, steps: int = 4, cache_path: str | None = DEFAULT_CACHE, candidates=None, force: bool = False) -> dict:
-    """Times the candidates on `runs` (their state advances by the timed
-    steps), sets the fastest process-wide and returns a report."""
+    """Times candidates on `runs` (their state advances by the timed steps),
+    sets the fastest process-wide and returns a report.  With `candidates`
+    given, exactly those are timed; otherwise the search goes by stages: the
+    cluster path's threshold with the default shape, then the shape (shared-
+    memory threshold, warp classes, warps per block) with the best threshold,
+    then the fused steps with the best of both."""
     import torch
 
-    cands = candidates or CANDIDATES
     key = f"{torch.cuda.get_device_name()}|{signature(runs)}"
     cache = _load(cache_path) if cache_path else {}
     if not force and key in cache:
@@ -88,14 +105,20 @@ def tune(runs, steps: int = 4, cache_path: str | None = DEFAULT_CACHE, candidate
         return {"key": key, "best": best, "cached": True, "ms_per_step": cache[key].get("ms_per_step")}
     t0 = time.perf_counter()
     timings = []
-    for c in cands:
-        sdm.sdm_set_tuning(c)
-        timings.append((time_candidate(runs, steps), c))
+    if candidates:
+        best_ms, best = _search(runs, steps, candidates, timings)
+    else:
+        fuse0 = sdm.FUSE_STEPS_DEFAULT
+        _, b1 = _search(runs, steps, [dict(DEFAULT_SHAPE, mid_max_sd=m, fuse_steps=fuse0) for m in MID_CHOICES
+                                      if m == 0 or m >= DEFAULT_SHAPE["smem_max_sd"]], timings)
+        _, b2 = _search(runs, steps, [dict(c, mid_max_sd=b1["mid_max_sd"] if b1["mid_max_sd"] == 0 else
+                                           max(b1["mid_max_sd"], c["smem_max_sd"]), fuse_steps=fuse0)
+                                      for c in CANDIDATES], timings)
+        best_ms, best = _search(runs, steps, [dict(b2, fuse_steps=f) for f in FUSE_CHOICES], timings)
     timings.sort(key=lambda x: x[0])
-    best_ms, best = timings[0]
     sdm.sdm_set_tuning(best)
     report = {"key": key, "best": best, "cached": False, "ms_per_step": best_ms,
-              "worst_ms_per_step": timings[-1][0], "candidates": len(cands), "tuning_s": time.perf_counter() - t0}
+              "worst_ms_per_step": timings[-1][0], "candidates": len(timings), "tuning_s": time.perf_counter() - t0}
     if cache_path:
         cache[key] = {"best": best, "ms_per_step": best_ms,
                       "all": [{"ms_per_step": t, **c} for t, c in timings]}

@@ -16,6 +16,7 @@
 
 #include "../../include/sdm.h"
 #include "sdm_kernels.cuh"
+#include "sdm_mid.cuh"
 
 using namespace sdm;
 
@@ -145,6 +146,11 @@ struct Plan {
     WorkItem *d_items[kNumClass] = {};
     int n_items[kNumClass] = {};
     int variant[kNumClass] = {};
+    WorkItem *d_mid[3] = {};     // cells of the cluster path, by cluster size K = 1, 2, 4, largest first
+    int n_mid[3] = {};
+    int mid_clusters[3] = {};    // clusters of each launch: the SMs dealt in proportion to the classes' SDs
+    cudaStream_t mid_side[2] = {}; // the K = 2 and K = 4 launches run beside the K = 1 one
+    cudaEvent_t mid_fork = nullptr, mid_join[2] = {};
     BigCell *d_bigs = nullptr;
     int n_big = 0;
     BigChunk *d_chunks = nullptr;
@@ -284,6 +290,14 @@ void plan_free(Plan &pl, DevMem &mem)
 {
     for (Buf &b : pl.bufs)
         mem.put(b.p, b.bytes);
+    for (int k = 0; k < 2; ++k) {
+        if (pl.mid_side[k])
+            cudaStreamDestroy(pl.mid_side[k]);
+        if (pl.mid_join[k])
+            cudaEventDestroy(pl.mid_join[k]);
+    }
+    if (pl.mid_fork)
+        cudaEventDestroy(pl.mid_fork);
     pl = Plan{};
 }
 
@@ -370,7 +384,8 @@ struct DevGrids {
     cudaError_t status = cudaSuccess;
     int variant[kNumVariants] = {};
     int fused[kNumFused] = {};
-    int spec = 1; // blocks of the total-spectrum kernel
+    int mid[3] = {}; // clusters of the mid-size-cell kernel resident at once, K = 1, 2, 4
+    int spec = 1;    // blocks of the total-spectrum kernel
 };
 std::mutex g_dev_mutex;
 DevGrids g_dev[kMaxDevices];
@@ -385,12 +400,12 @@ const DevGrids &dev_grids()
 }
 
 std::mutex g_tuning_mutex;
-sdm_tuning g_tuning = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT};
+sdm_tuning g_tuning = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT, SDM_MID_MAX_SD_DEFAULT};
 
 bool same_tuning(const sdm_tuning &a, const sdm_tuning &b)
 {
     return a.smem_max_sd == b.smem_max_sd && a.warp_cell_max == b.warp_cell_max &&
-           a.warps_per_block == b.warps_per_block && a.fuse_steps == b.fuse_steps;
+           a.warps_per_block == b.warps_per_block && a.fuse_steps == b.fuse_steps && a.mid_max_sd == b.mid_max_sd;
 }
 
 sdm_tuning current_tuning()
@@ -409,6 +424,50 @@ int variant_for(int cap, const sdm_tuning &t)
             return v;
     }
     return -1;
+}
+
+// The mid-size-cell kernel with K CTAs per cluster: its shared-memory limit,
+// and how many clusters fit on the device at once (its persistent grid).
+template <int K>
+cudaError_t mid_configure(int &clusters)
+{
+    cudaError_t r = cudaFuncSetAttribute(mid_cell_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)MidSmem<K>::bytes);
+    if (r != cudaSuccess)
+        return r;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(K, 1, 1);
+    cfg.blockDim = dim3(kMidNT, 1, 1);
+    cfg.dynamicSmemBytes = MidSmem<K>::bytes;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    r = cudaOccupancyMaxActiveClusters(&n, mid_cell_kernel<K>, &cfg);
+    clusters = n > 0 ? n : 1;
+    return r;
+}
+
+template <int K>
+cudaError_t launch_mid(int clusters, int n, const WorkItem *items, InstDev *const *insts, int64_t off, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(K * clusters, 1, 1);
+    cfg.blockDim = dim3(kMidNT, 1, 1);
+    cfg.dynamicSmemBytes = MidSmem<K>::bytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, mid_cell_kernel<K>, items, (int32_t)n, insts, off);
 }
 
 // Configures the current device once (the first context, batch or spectrum
@@ -483,6 +542,9 @@ cudaError_t configure_kernels()
         if ((r = cudaFuncSetAttribute(big_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
         if ((r = cudaFuncSetAttribute(big_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, hb)) != cudaSuccess) e = r;
+        if ((r = mid_configure<1>(G.mid[0])) != cudaSuccess) e = r;
+        if ((r = mid_configure<2>(G.mid[1])) != cudaSuccess) e = r;
+        if ((r = mid_configure<4>(G.mid[2])) != cudaSuccess) e = r;
         return e;
     }();
     G.done = true;
@@ -514,6 +576,7 @@ sdm_status build_plan(sdm_batch *b)
     DevMem &mem = b->mem;
     const int n_inst = (int)b->ctxs.size();
     std::vector<WorkItem> items[kNumClass];
+    std::vector<WorkItem> mid[3];
     std::vector<BigCell> bigs;
     std::vector<BigChunk> chunks;
     std::vector<BigBucket> buckets;
@@ -543,6 +606,11 @@ sdm_status build_plan(sdm_batch *b)
                 items[cls].push_back(WorkItem{i, c->cfg.cell_base + cell, c->h_cell_off[cell], n});
                 continue;
             }
+            if (n <= tun.mid_max_sd) { // the cluster path, K = 1, 2 or 4 CTAs (sorted below)
+                const int km = n <= kMidSdPerCta ? 0 : (n <= 2 * kMidSdPerCta ? 1 : 2);
+                mid[km].push_back(WorkItem{i, c->cfg.cell_base + cell, c->h_cell_off[cell], n});
+                continue;
+            }
             BigCell bc{};
             bc.inst = i;
             bc.cell = cell;
@@ -568,6 +636,8 @@ sdm_status build_plan(sdm_batch *b)
             bigs.push_back(bc);
         }
     }
+    for (int k = 0; k < 3; ++k) // largest cells first (the kernel deals them in a snake order)
+        std::stable_sort(mid[k].begin(), mid[k].end(), [](const WorkItem &a, const WorkItem &c) { return a.n > c.n; });
     // every table (the runs, the work list of each class, the big-cell
     // descriptors) in one host buffer, one device buffer and one copy
     pl.n_inst = n_inst;
@@ -576,6 +646,11 @@ sdm_status build_plan(sdm_batch *b)
     for (int k = 0; k < kNumClass; ++k) {
         off_items[k] = sz;
         sz += a16(sizeof(WorkItem) * items[k].size());
+    }
+    size_t off_mid[3];
+    for (int k = 0; k < 3; ++k) {
+        off_mid[k] = sz;
+        sz += a16(sizeof(WorkItem) * mid[k].size());
     }
     const size_t off_bigs = sz;
     sz += a16(sizeof(BigCell) * bigs.size());
@@ -591,6 +666,9 @@ sdm_status build_plan(sdm_batch *b)
     for (int k = 0; k < kNumClass; ++k)
         if (!items[k].empty())
             std::memcpy(h + off_items[k], items[k].data(), sizeof(WorkItem) * items[k].size());
+    for (int k = 0; k < 3; ++k)
+        if (!mid[k].empty())
+            std::memcpy(h + off_mid[k], mid[k].data(), sizeof(WorkItem) * mid[k].size());
     if (!bigs.empty()) {
         std::memcpy(h + off_bigs, bigs.data(), sizeof(BigCell) * bigs.size());
         std::memcpy(h + off_chunks, chunks.data(), sizeof(BigChunk) * chunks.size());
@@ -604,6 +682,43 @@ sdm_status build_plan(sdm_batch *b)
     for (int k = 0; k < kNumClass; ++k) {
         pl.n_items[k] = (int)items[k].size();
         pl.d_items[k] = pl.n_items[k] ? reinterpret_cast<WorkItem *>(d + off_items[k]) : nullptr;
+    }
+    for (int k = 0; k < 3; ++k) {
+        pl.n_mid[k] = (int)mid[k].size();
+        pl.d_mid[k] = pl.n_mid[k] ? reinterpret_cast<WorkItem *>(d + off_mid[k]) : nullptr;
+    }
+    {
+        // the device's SMs (one cluster-path CTA each) dealt to the classes in
+        // proportion to their SDs, at least one cluster to each class with
+        // cells, at most one per cell and no more than fit at once
+        const DevGrids &G = dev_grids();
+        int64_t work[3] = {}, total = 0;
+        for (int k = 0; k < 3; ++k) {
+            for (const WorkItem &w : mid[k])
+                work[k] += w.n;
+            total += work[k];
+        }
+        const int ks[3] = {1, 2, 4};
+        const int sms = G.mid[0];
+        for (int k = 0; k < 3; ++k) {
+            if (!pl.n_mid[k])
+                continue;
+            const int share = (int)((double)sms * (double)work[k] / (double)total) / ks[k];
+            pl.mid_clusters[k] = std::max(1, std::min({share, pl.n_mid[k], G.mid[k]}));
+        }
+        int classes = 0;
+        for (int k = 0; k < 3; ++k)
+            classes += pl.n_mid[k] ? 1 : 0;
+        if (classes > 1) {
+            cudaError_t e = cudaEventCreateWithFlags(&pl.mid_fork, cudaEventDisableTiming);
+            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+                e = cudaStreamCreateWithFlags(&pl.mid_side[k], cudaStreamNonBlocking);
+                if (e == cudaSuccess)
+                    e = cudaEventCreateWithFlags(&pl.mid_join[k], cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "batch plan: side streams");
+        }
     }
     if (!bigs.empty()) {
         pl.n_big = (int)bigs.size();
@@ -632,9 +747,30 @@ sdm_status build_plan(sdm_batch *b)
 }
 
 // One step (offset `off` from each run's device counter) of every cell above
-// the shared-memory threshold.
+// the shared-memory threshold: the cluster path, then the multi-pass path.
 void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
 {
+    // the three cluster sizes side by side (fork and join by events; a graph
+    // captures the same): each on its share of the SMs
+    const bool fork = pl.mid_fork != nullptr;
+    cudaStream_t s2 = fork ? pl.mid_side[0] : st, s4 = fork ? pl.mid_side[1] : st;
+    if (fork) {
+        cudaEventRecord(pl.mid_fork, st);
+        cudaStreamWaitEvent(s2, pl.mid_fork, 0);
+        cudaStreamWaitEvent(s4, pl.mid_fork, 0);
+    }
+    if (pl.n_mid[2])
+        launch_mid<4>(pl.mid_clusters[2], pl.n_mid[2], pl.d_mid[2], pl.d_insts, off, s4);
+    if (pl.n_mid[1])
+        launch_mid<2>(pl.mid_clusters[1], pl.n_mid[1], pl.d_mid[1], pl.d_insts, off, s2);
+    if (pl.n_mid[0])
+        launch_mid<1>(pl.mid_clusters[0], pl.n_mid[0], pl.d_mid[0], pl.d_insts, off, st);
+    if (fork) {
+        cudaEventRecord(pl.mid_join[0], s2);
+        cudaEventRecord(pl.mid_join[1], s4);
+        cudaStreamWaitEvent(st, pl.mid_join[0], 0);
+        cudaStreamWaitEvent(st, pl.mid_join[1], 0);
+    }
     if (pl.n_big) {
         const size_t hs = big_hist_smem(pl.max_big_lb);
         big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
@@ -915,6 +1051,10 @@ sdm_status check_device_status(sdm_ctx *ctx)
         return cuda_fail(ctx, e, "status read");
     if (status & 1u)
         return fail(&ctx->error, SDM_ETIMEOUT, "a device-side wait for a bulk copy gave up; results are incomplete");
+    if (status & 2u)
+        return fail(&ctx->error, SDM_ESTATE,
+                    "a sort bucket of a mid-size cell outgrew its room (more than 2048 of the cell's keys in one "
+                    "bucket): that cell was not stepped; results are incomplete");
     return SDM_OK;
 }
 
@@ -1434,7 +1574,7 @@ sdm_status sdm_batch_destroy(sdm_batch *batch)
 
 sdm_status sdm_set_tuning(const sdm_tuning *t)
 {
-    sdm_tuning v = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT};
+    sdm_tuning v = {4096, 512, 2, SDM_FUSE_STEPS_DEFAULT, SDM_MID_MAX_SD_DEFAULT};
     if (t) {
         const bool smem_ok = t->smem_max_sd == 512 || t->smem_max_sd == 1024 || t->smem_max_sd == 2048 ||
                              t->smem_max_sd == 4096;
@@ -1442,10 +1582,12 @@ sdm_status sdm_set_tuning(const sdm_tuning *t)
                              t->warp_cell_max == 256 || t->warp_cell_max == 512;
         const bool wpb_ok = t->warps_per_block == 1 || t->warps_per_block == 2 || t->warps_per_block == 4;
         const bool fuse_ok = t->fuse_steps >= 0 && t->fuse_steps <= 1024;
-        if (!smem_ok || !warp_ok || !wpb_ok || !fuse_ok || t->warp_cell_max > t->smem_max_sd)
+        const bool mid_ok = t->mid_max_sd == 0 || (t->mid_max_sd >= t->smem_max_sd && t->mid_max_sd <= kMidMaxSd);
+        if (!smem_ok || !warp_ok || !wpb_ok || !fuse_ok || !mid_ok || t->warp_cell_max > t->smem_max_sd)
             return fail(nullptr, SDM_EINVAL,
                         "tuning: smem_max_sd in {512,1024,2048,4096}, warp_cell_max in {0,64,128,256,512} and <= "
-                        "smem_max_sd, warps_per_block in {1,2,4}, fuse_steps in 0..1024");
+                        "smem_max_sd, warps_per_block in {1,2,4}, fuse_steps in 0..1024, mid_max_sd 0 or in "
+                        "[smem_max_sd, 65536]");
         v = *t;
     }
     std::lock_guard<std::mutex> lock(g_tuning_mutex);

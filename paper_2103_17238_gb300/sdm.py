@@ -70,6 +70,7 @@ class sdm_config(ctypes.Structure):
 
 
 FUSE_STEPS_DEFAULT = 64  # SDM_FUSE_STEPS_DEFAULT of the header
+MID_MAX_SD_DEFAULT = 16384  # SDM_MID_MAX_SD_DEFAULT of the header
 
 
 class sdm_tuning(ctypes.Structure):
@@ -78,6 +79,7 @@ class sdm_tuning(ctypes.Structure):
         ("warp_cell_max", ctypes.c_int32),
         ("warps_per_block", ctypes.c_int32),
         ("fuse_steps", ctypes.c_int32),
+        ("mid_max_sd", ctypes.c_int32),
     ]
 
 
@@ -421,7 +423,7 @@ def sdm_set_tuning(tuning=None):
         _check(load().sdm_set_tuning(None), "sdm_set_tuning")
         return
     t = sdm_tuning(int(tuning["smem_max_sd"]), int(tuning["warp_cell_max"]), int(tuning["warps_per_block"]),
-                   int(tuning.get("fuse_steps", FUSE_STEPS_DEFAULT)))
+                   int(tuning.get("fuse_steps", FUSE_STEPS_DEFAULT)), int(tuning.get("mid_max_sd", MID_MAX_SD_DEFAULT)))
     _check(load().sdm_set_tuning(ctypes.byref(t)), "sdm_set_tuning")
 
 
@@ -429,7 +431,7 @@ def sdm_get_tuning() -> dict:
     t = sdm_tuning()
     _check(load().sdm_get_tuning(ctypes.byref(t)), "sdm_get_tuning")
     return {"smem_max_sd": t.smem_max_sd, "warp_cell_max": t.warp_cell_max, "warps_per_block": t.warps_per_block,
-            "fuse_steps": t.fuse_steps}
+            "fuse_steps": t.fuse_steps, "mid_max_sd": t.mid_max_sd}
 
 
 # ------------------------------------------------------------ owners

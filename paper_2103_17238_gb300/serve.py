@@ -56,13 +56,16 @@ def make_run(inst: I.Instance) -> sdm.Run:
 
 class Server:
     def __init__(self, budget_bytes: int, chunk: int = 20, keep_state: bool = False, use_graph: bool = False,
-                 time_scale: float = 1.0, fuse_steps: int | None = None):
+                 time_scale: float = 1.0, fuse_steps: int | None = None, admit_per_pass: int = 8):
         self.budget = int(budget_bytes)
         self.chunk = int(chunk)
         self.fuse_steps = fuse_steps  # None: the process-wide tuning as it is
         self.keep_state = keep_state
         self.use_graph = use_graph
         self.time_scale = time_scale  # arrival times are divided by this
+        # requests admitted per pass: a burst of arrivals is admitted a few at
+        # a time, each pass overlapping a tick of the runs already admitted
+        self.admit_per_pass = max(1, int(admit_per_pass))
 
     def _batch(self, runs):
         """A batch of the active runs; its launch plan takes the tuning of the
@@ -110,7 +113,10 @@ class Server:
         def admit():
             nonlocal used, max_used
             now = (time.perf_counter() - t0) * self.time_scale
-            while pending and pending[0].req.arrival <= now and used + pending[0].footprint <= self.budget:
+            took = 0
+            while (pending and took < self.admit_per_pass and pending[0].req.arrival <= now
+                   and used + pending[0].footprint <= self.budget):
+                took += 1
                 s = pending.pop(0)
                 with torch.cuda.stream(admit_stream):
                     s.run = make_run(s.req.inst)  # returns after its upload has landed

@@ -107,16 +107,17 @@ def test_tuning_round_trip_and_validation(lib):
     from paper_2103_17238_gb300 import sdm
 
     default = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2,
-               "fuse_steps": sdm.FUSE_STEPS_DEFAULT}
+               "fuse_steps": sdm.FUSE_STEPS_DEFAULT, "mid_max_sd": sdm.MID_MAX_SD_DEFAULT}
     sdm.sdm_set_tuning(None)
     assert sdm.sdm_get_tuning() == default
-    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": sdm.FUSE_STEPS_DEFAULT}
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": sdm.FUSE_STEPS_DEFAULT,
+         "mid_max_sd": sdm.MID_MAX_SD_DEFAULT}
     sdm.sdm_set_tuning({k: t[k] for k in ("smem_max_sd", "warp_cell_max", "warps_per_block")})
     assert sdm.sdm_get_tuning() == t
-    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 1024}
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 1024, "mid_max_sd": 0}
     sdm.sdm_set_tuning(t)
     assert sdm.sdm_get_tuning() == t
-    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 0}
+    t = {"smem_max_sd": 1024, "warp_cell_max": 128, "warps_per_block": 4, "fuse_steps": 0, "mid_max_sd": 20000}
     sdm.sdm_set_tuning(t)
     assert sdm.sdm_get_tuning() == t
     for bad in ({"smem_max_sd": 8192, "warp_cell_max": 256, "warps_per_block": 2},
@@ -127,6 +128,8 @@ def test_tuning_round_trip_and_validation(lib):
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 3},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 0},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "fuse_steps": 1025},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "mid_max_sd": 70000},
+                {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "mid_max_sd": 2048},
                 {"smem_max_sd": 4096, "warp_cell_max": 256, "warps_per_block": 2, "fuse_steps": -1}):
         with pytest.raises(sdm.SdmError) as e:
             sdm.sdm_set_tuning(bad)

@@ -1,8 +1,8 @@
 """The launch tuning changes how cells are mapped to kernels, never the
 result: every setting must give the oracle's state bit for bit, for cells of
-every size class (and the multi-pass path above the shared-memory
-threshold), alone and in a batch; the autotuner picks one of its candidates
-and caches it."""
+every size class (and the cluster or the multi-pass path above the
+shared-memory threshold), alone and in a batch; the autotuner picks one of
+its candidates and caches it."""
 import itertools
 import json
 
@@ -19,10 +19,13 @@ SIZES = [0, 1, 2, 3, 31, 33, 64, 65, 128, 129, 255, 256, 257, 511, 512, 513, 102
 TUNINGS = [dict(smem_max_sd=s, warp_cell_max=w, warps_per_block=k)
            for s, w, k in itertools.product((512, 1024, 2048, 4096), (0, 64, 128, 256, 512), (1, 2, 4))
            if not (w == 0 and k != 2)]
-# every other setting with one launch per step, the rest with the default fusion
+# every other setting with one launch per step, the rest with the default fusion;
+# every third with the cells above the shared-memory threshold on the multi-pass
+# path instead of the cluster path
 for _i, _t in enumerate(TUNINGS):
     if _i % 2:
         _t["fuse_steps"] = 0
+    _t["mid_max_sd"] = 0 if _i % 3 == 0 else 65536
 
 
 @pytest.fixture(scope="module")
@@ -96,7 +99,8 @@ def test_autotuned_batch_equals_default(env, tmp_path):
     probe = make()
     rep = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert not rep["cached"] and rep["best"] in cands
-    assert sdm.sdm_get_tuning() == {"fuse_steps": sdm.FUSE_STEPS_DEFAULT, **rep["best"]}
+    assert sdm.sdm_get_tuning() == {"fuse_steps": sdm.FUSE_STEPS_DEFAULT, "mid_max_sd": sdm.MID_MAX_SD_DEFAULT,
+                                    **rep["best"]}
     assert rep["ms_per_step"] <= rep["worst_ms_per_step"]
     again = autotune.tune(probe, steps=2, cache_path=cache, candidates=cands)
     assert again["cached"] and again["best"] == rep["best"]
