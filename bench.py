@@ -387,7 +387,21 @@ def measure_e2e(args, g, sdm, torch, pairs0):
     dt_run = time.perf_counter() - t0
     run.close()
     h2d = g.n_sd * (8 + 8 + 4)
+    # the host link itself: one plain pinned copy of the same bytes, for scale
+    dev = torch.device("cuda", torch.cuda.current_device())
+    src = torch.empty(h2d, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(h2d, dtype=torch.uint8, device=dev)
+    dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        dst.copy_(src, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    link_gbs = 5 * h2d / (e0.elapsed_time(e1) * 1e-3) / 1e9
     return {"value": pairs0 / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "pinned_h2d_copy_gbs": link_gbs,
             "d2h_bytes_per_step": 8 * (len(I.R_EDGES) - 1), "ms_per_step": dt * 1e3, "steps": n,
             "whole_run": {"steps": steps, "ms": dt_run * 1e3, "ms_per_step": dt_run * 1e3 / steps,
                           "pair_updates_per_s": pairs_run / dt_run,

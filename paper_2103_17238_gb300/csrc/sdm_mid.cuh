@@ -30,6 +30,7 @@
 namespace sdm {
 
 constexpr int kMidNT = 1024;
+static_assert(kMidNT % 32 == 0 && kMidNT <= 1024 && ((4 << 11) / 4) % kMidNT == 0, "mid kernel: block shape");
 constexpr int kMidSdPerCta = 16384; // stored SDs per CTA at most
 constexpr int kMidMaxSd = 4 * kMidSdPerCta;
 constexpr int kMidLBCta = 11;       // 2048 buckets per CTA
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kMidNT, 1) mid_cell_kernel(const WorkItem *__r
             s_warp[warp] = incl;
         __syncthreads();
         if (warp == 0) {
-            uint32_t v = s_warp[lane], vi = v;
+            uint32_t v = lane < kMidNT / 32 ? s_warp[lane] : 0u, vi = v;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const uint32_t y = __shfl_up_sync(FULL, vi, d);
@@ -341,10 +342,11 @@ __global__ void __launch_bounds__(kMidNT, 1) mid_cell_kernel(const WorkItem *__r
             const float sc = C.dtdvf * ratio_f;
             const uint32_t l_lo = p_lo / 2, l_hi = min(n_pairs, (p_hi + 1) / 2);
             for (uint32_t q = (l_lo >> 1) + t; 2 * q < l_hi; q += kMidNT) {
-                // both pairs' ranks and multiplicities first: their loads overlap
-                // the Philox block
+                // both pairs' ranks, then every multiplicity and volume they
+                // need, in one round of loads that overlaps the Philox block
                 uint32_t ra[2], rb[2];
                 int64_t x0[2], x1[2];
+                double v0[2], v1[2];
                 bool in[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -352,8 +354,13 @@ __global__ void __launch_bounds__(kMidNT, 1) mid_cell_kernel(const WorkItem *__r
                     in[h] = l >= l_lo && l < l_hi;
                     ra[h] = in[h] ? entry(2 * l) : 0u;
                     rb[h] = in[h] ? entry(2 * l + 1) : 0u;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
                     x0[h] = in[h] ? gxi[ra[h]] : 0;
                     x1[h] = in[h] ? gxi[rb[h]] : 0;
+                    v0[h] = in[h] ? gv[ra[h]] : 1.0;
+                    v1[h] = in[h] ? gv[rb[h]] : 1.0;
                 }
                 const uint4 w = draw4(seed, q, cell, s, 1u);
 #pragma unroll
@@ -363,6 +370,7 @@ __global__ void __launch_bounds__(kMidNT, 1) mid_cell_kernel(const WorkItem *__r
                     uint32_t a = ra[h], b = rb[h];
                     const uint32_t wa = h ? w.z : w.x, wb = h ? w.w : w.y;
                     int64_t xa = x0[h], xb = x1[h];
+                    double va = v0[h], vb = v1[h];
                     if (xa < xb) { // j holds the larger multiplicity; ties keep the earlier
                         const uint32_t tr = a;
                         a = b;
@@ -370,8 +378,10 @@ __global__ void __launch_bounds__(kMidNT, 1) mid_cell_kernel(const WorkItem *__r
                         const int64_t tx = xa;
                         xa = xb;
                         xb = tx;
+                        const double tv = va;
+                        va = vb;
+                        vb = tv;
                     }
-                    double va = gv[a], vb = gv[b];
                     const uint32_t ha = (uint32_t)__double2hiint(va), hb = (uint32_t)__double2hiint(vb);
                     if (pair_prefilter_zero(C, sc, xa, ha, hb, wa))
                         continue;
