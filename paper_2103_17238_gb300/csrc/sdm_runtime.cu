@@ -149,8 +149,8 @@ struct Plan {
     WorkItem *d_mid[3] = {};     // cells of the cluster path, by cluster size K = 1, 2, 4, largest first
     int n_mid[3] = {};
     int mid_clusters[3] = {};    // clusters of each launch: the SMs dealt in proportion to the classes' SDs
-    cudaStream_t mid_side[2] = {}; // the K = 2 and K = 4 launches run beside the K = 1 one
-    cudaEvent_t mid_fork = nullptr, mid_join[2] = {};
+    cudaStream_t mid_side[3] = {}; // the cluster launches run beside each other and the multi-pass path
+    cudaEvent_t mid_fork = nullptr, mid_join[3] = {};
     BigCell *d_bigs = nullptr;
     int n_big = 0;
     BigChunk *d_chunks = nullptr;
@@ -290,7 +290,7 @@ void plan_free(Plan &pl, DevMem &mem)
 {
     for (Buf &b : pl.bufs)
         mem.put(b.p, b.bytes);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 3; ++k) {
         if (pl.mid_side[k])
             cudaStreamDestroy(pl.mid_side[k]);
         if (pl.mid_join[k])
@@ -689,10 +689,11 @@ sdm_status build_plan(sdm_batch *b)
     }
     {
         // the device's SMs (one cluster-path CTA each) dealt to the classes in
-        // proportion to their SDs, at least one cluster to each class with
-        // cells, at most one per cell and no more than fit at once
+        // proportion to their SDs (the multi-pass path's cells, which run beside
+        // them, count too), at least one cluster to each class with cells, at
+        // most one per cell and no more than fit at once
         const DevGrids &G = dev_grids();
-        int64_t work[3] = {}, total = 0;
+        int64_t work[3] = {}, total = sd_total;
         for (int k = 0; k < 3; ++k) {
             for (const WorkItem &w : mid[k])
                 work[k] += w.n;
@@ -706,12 +707,12 @@ sdm_status build_plan(sdm_batch *b)
             const int share = (int)((double)sms * (double)work[k] / (double)total) / ks[k];
             pl.mid_clusters[k] = std::max(1, std::min({share, pl.n_mid[k], G.mid[k]}));
         }
-        int classes = 0;
+        int classes = bigs.empty() ? 0 : 1;
         for (int k = 0; k < 3; ++k)
             classes += pl.n_mid[k] ? 1 : 0;
         if (classes > 1) {
             cudaError_t e = cudaEventCreateWithFlags(&pl.mid_fork, cudaEventDisableTiming);
-            for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
                 e = cudaStreamCreateWithFlags(&pl.mid_side[k], cudaStreamNonBlocking);
                 if (e == cudaSuccess)
                     e = cudaEventCreateWithFlags(&pl.mid_join[k], cudaEventDisableTiming);
@@ -750,28 +751,37 @@ sdm_status build_plan(sdm_batch *b)
 // the shared-memory threshold: the cluster path, then the multi-pass path.
 void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
 {
-    // the three cluster sizes side by side (fork and join by events; a graph
-    // captures the same): each on its share of the SMs
+    // the cluster sizes side by side, and beside the multi-pass path (fork
+    // and join by events; a graph captures the same): each cluster size on
+    // its share of the SMs, the multi-pass kernels on the rest
     const bool fork = pl.mid_fork != nullptr;
-    cudaStream_t s2 = fork ? pl.mid_side[0] : st, s4 = fork ? pl.mid_side[1] : st;
     if (fork) {
         cudaEventRecord(pl.mid_fork, st);
-        cudaStreamWaitEvent(s2, pl.mid_fork, 0);
-        cudaStreamWaitEvent(s4, pl.mid_fork, 0);
+        for (int k = 0; k < 3; ++k)
+            if (pl.n_mid[k])
+                cudaStreamWaitEvent(pl.mid_side[k], pl.mid_fork, 0);
     }
+    auto side = [&](int k) { return fork ? pl.mid_side[k] : st; };
     if (pl.n_mid[2])
-        launch_mid<4>(pl.mid_clusters[2], pl.n_mid[2], pl.d_mid[2], pl.d_insts, off, s4);
+        launch_mid<4>(pl.mid_clusters[2], pl.n_mid[2], pl.d_mid[2], pl.d_insts, off, side(2));
     if (pl.n_mid[1])
-        launch_mid<2>(pl.mid_clusters[1], pl.n_mid[1], pl.d_mid[1], pl.d_insts, off, s2);
+        launch_mid<2>(pl.mid_clusters[1], pl.n_mid[1], pl.d_mid[1], pl.d_insts, off, side(1));
     if (pl.n_mid[0])
-        launch_mid<1>(pl.mid_clusters[0], pl.n_mid[0], pl.d_mid[0], pl.d_insts, off, st);
-    if (fork) {
-        cudaEventRecord(pl.mid_join[0], s2);
-        cudaEventRecord(pl.mid_join[1], s4);
-        cudaStreamWaitEvent(st, pl.mid_join[0], 0);
-        cudaStreamWaitEvent(st, pl.mid_join[1], 0);
+        launch_mid<1>(pl.mid_clusters[0], pl.n_mid[0], pl.d_mid[0], pl.d_insts, off, side(0));
+    auto join = [&]() {
+        if (!fork)
+            return;
+        for (int k = 0; k < 3; ++k)
+            if (pl.n_mid[k]) {
+                cudaEventRecord(pl.mid_join[k], pl.mid_side[k]);
+                cudaStreamWaitEvent(st, pl.mid_join[k], 0);
+            }
+    };
+    if (!pl.n_big) {
+        join();
+        return;
     }
-    if (pl.n_big) {
+    {
         const size_t hs = big_hist_smem(pl.max_big_lb);
         big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
         const int tiles = std::max(1, (1 << pl.max_big_lb) / kBigColNT);
@@ -782,6 +792,7 @@ void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
                                                                    off);
         big_pairs_kernel<<<pl.n_pair_blocks, kPairNT, 0, st>>>(pl.d_pairs, pl.d_bigs, pl.d_insts, pl.scratch, off);
     }
+    join();
 }
 
 // Enqueues one step (offset `off` from each run's device counter) of every cell.
