@@ -53,7 +53,7 @@ KERNEL_NAME = "warp_cell_step_kernel<256,2,2>"
 PROFILE = os.path.join(ROOT, "profiles", "cell_step_kernel_grid_geometric_4M.md")
 L2_FLUSH_BYTES = 256 << 20
 EXTRAS = ("batched_vs_plain", "large_cells", "kfp32", "fused", "serving", "sedimentation", "long_kernel",
-          "paper_setting", "condensation")
+          "paper_setting", "condensation", "mid_cells")
 
 
 # The step kernel and every helper it uses: the device header, and the kernel
@@ -324,6 +324,8 @@ def run_ours(args, rank: int, world: int):
             extras["paper_setting"] = measure_paper_setting(sdm, torch)
         if "condensation" in wanted:
             extras["condensation"] = measure_condensation(sdm, torch, g)
+        if "mid_cells" in wanted:
+            extras["mid_cells"] = measure_mid_cells(sdm, torch)
     res = None
     if rank == 0:
         res = {
@@ -588,6 +590,40 @@ def measure_fused(sdm, torch, g, steps=600):
                 ref = (xi, v)
             else:
                 out[key + "_state_identical"] = bool(np.array_equal(xi, ref[0]) and np.array_equal(v, ref[1]))
+    finally:
+        sdm.sdm_set_tuning(None)
+    return out
+
+
+def measure_mid_cells(sdm, torch, steps=10):
+    """Mid-size cells, one cluster size at a time, filling the GPU once: 152
+    Golovin boxes of 12,000 SDs (one CTA each), 72 of 24,000 (clusters of
+    2), 36 of 60,000 (clusters of 4; 36 such clusters fit at once), each
+    through the cluster path and through the multi-pass global path
+    (tuning mid_max_sd 65536 and 0, one launch per step).  The states of the
+    two paths are compared bit for bit."""
+    out = {"workload": "Golovin boxes (b=1500 s^-1, dV=1e6 m^3), one cell each, seeds 0.., one launch per step",
+           "steps": steps}
+    base = {"smem_max_sd": 4096, "warp_cell_max": 512, "warps_per_block": 2, "fuse_steps": 0}
+    try:
+        for n_sd, cells, k in ((12000, 152, 1), (24000, 72, 2), (60000, 36, 4)):
+            res, states = {}, []
+            for name, mid in (("cluster", 65536), ("multi_pass", 0)):
+                sdm.sdm_set_tuning({**base, "mid_max_sd": mid})
+                runs = [sdm.Run(sdm.make_config("golovin", dv=I.DV_BOX, seed=c), n_sd).set_attributes(
+                    *(lambda t: (t.xi, t.v, t.cell))(I.box_golovin(n_sd, seed=c))) for c in range(cells)]
+                batch = sdm.Batch(runs)
+                batch.step(2)
+                dt = _timed(torch, lambda: batch.step(steps))
+                batch.close()
+                states.append([r.attributes() for r in runs[:8]])
+                for r in runs:
+                    r.close()
+                res[name + "_us_per_step"] = dt / steps * 1e6
+                res[name + "_pair_updates_per_s"] = cells * (n_sd // 2) * steps / dt
+            res["identical"] = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+                                   for a, b in zip(*states))
+            out[f"K{k}_{cells}x{n_sd}"] = res
     finally:
         sdm.sdm_set_tuning(None)
     return out

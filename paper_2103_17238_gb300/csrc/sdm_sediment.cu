@@ -239,37 +239,68 @@ __global__ void __launch_bounds__(kSedNT) sed_move_kernel(const InstDev *__restr
 
 // One block: ustart = exclusive scan of counts[0 .. n_groups) (total at
 // ustart[n_groups]); poff the same with every count rounded up to even;
-// *precip_total = sum of precip[0 .. n_parts) in a fixed order.
+// *precip_total = sum of precip[0 .. n_parts) in a fixed order.  Both scans
+// run at once on packed 64-bit sums (unpadded below, padded above: neither
+// exceeds 2^31), 8 consecutive groups per thread, tiles of 8192 groups.
 __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restrict__ counts, int32_t n_groups,
                                                         int32_t *__restrict__ ustart, int32_t *__restrict__ poff,
                                                         const double *__restrict__ precip, int32_t n_parts,
                                                         double *__restrict__ precip_total)
 {
-    __shared__ uint32_t s_u[1024], s_p[1024];
-    __shared__ uint32_t s_warp[32];
+    constexpr int E = 8, TILE = 1024 * E;
+    __shared__ uint32_t s_c[TILE];
+    __shared__ unsigned long long s_w[32];
     __shared__ double s_pr[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    // tiles of 1024 groups (coalesced), running totals carried over
-    uint32_t cu = 0, cp = 0;
-    for (int32_t g0 = 0; g0 < n_groups; g0 += 1024) {
-        const int32_t g = g0 + t;
-        const uint32_t c = g < n_groups ? counts[g] : 0u;
-        s_u[t] = c;
-        s_p[t] = (c + 1u) & ~1u;
+    unsigned long long carry = 0;
+    for (int32_t g0 = 0; g0 < n_groups; g0 += TILE) {
+        for (int i = t; i < TILE; i += 1024)
+            s_c[i] = g0 + i < n_groups ? counts[g0 + i] : 0u;
         __syncthreads();
-        const uint32_t tu = block_exclusive_scan<1024, 1024>(s_u, s_warp);
-        const uint32_t tp = block_exclusive_scan<1024, 1024>(s_p, s_warp);
-        if (g < n_groups) {
-            ustart[g] = (int32_t)(cu + s_u[t]);
-            poff[g] = (int32_t)(cp + s_p[t]);
+        unsigned long long v[E], sum = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const uint32_t c = s_c[t * E + e];
+            v[e] = (unsigned long long)c | ((unsigned long long)((c + 1u) & ~1u) << 32);
+            sum += v[e];
         }
-        cu += tu;
-        cp += tp;
+        unsigned long long x = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d)
+                x += y;
+        }
+        if (lane == 31)
+            s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_w[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+                if (lane >= d)
+                    w += y;
+            }
+            s_w[lane] = w; // inclusive totals of warps 0 .. lane
+        }
+        __syncthreads();
+        unsigned long long base = carry + (warp > 0 ? s_w[warp - 1] : 0ull) + x - sum;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int32_t g = g0 + t * E + e;
+            if (g < n_groups) {
+                ustart[g] = (int32_t)(uint32_t)base;
+                poff[g] = (int32_t)(uint32_t)(base >> 32);
+            }
+            base += v[e];
+        }
+        carry += s_w[31];
         __syncthreads();
     }
     if (t == 0) {
-        ustart[n_groups] = (int32_t)cu;
-        poff[n_groups] = (int32_t)cp;
+        ustart[n_groups] = (int32_t)(uint32_t)carry;
+        poff[n_groups] = (int32_t)(uint32_t)(carry >> 32);
     }
     // the precipitated water: thread t sums parts t, t + 1024, ... in order,
     // then a fixed tree over the threads
