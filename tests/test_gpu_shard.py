@@ -82,6 +82,43 @@ def test_pieces_equal_the_whole_grid(env, n_pieces, kernel):
     assert pr > 0 and int((st.xi[inside] != xi[inside]).sum()) > 0
 
 
+def test_a_piece_that_starts_empty(env):
+    """The lowest piece's levels start without SDs; large drops fall into
+    them from above, so that piece's context starts stepping mid-run (at the
+    grid's step index, so its random streams are the grid's)."""
+    O, sdm, S, torch = env
+    xi, v, cell, zeta = _initial(O, 21)
+    keep = cell // NX >= 6  # levels 0..5 empty
+    xi, v, cell, zeta = xi[keep], v[keep], cell[keep], zeta[keep]
+    gid = np.arange(len(xi), dtype=np.int64)
+    geom = S.Geometry(NX, NZ, DZ)
+    n_pieces = 3  # levels [0, 5), [5, 11), [11, 16)
+    parts = S.split_state(gid, xi, v, cell, zeta, NX, S.level_ranges(NZ, n_pieces))
+    assert len(parts[0]) == 0
+    run = S.ShardedRun(geom, n_pieces, S.LoopbackComm(),
+                       lambda i, lo, hi, rec: S.LibPiece(geom, lo, hi, rec, len(xi), kernel="geometric", dv=1e-1,
+                                                         dt=DT, seed=5)).start(parts)
+    cycles = 5
+    for k in range(cycles):
+        run.coalesce(1)  # coalescence first here: the empty piece counts the steps it skips
+        run.sediment()
+    got = run.state()
+    run.close()
+    P = O.params("geometric", dv=1e-1, dt=DT, seed=5)
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, NX * NZ)
+    zt = zeta.copy()
+    for k in range(cycles):
+        O.step(P, st, k)
+        O.sediment(P, st, NX, DZ, zt)
+    inside = np.nonzero(st.cell >= 0)[0]
+    assert np.any(st.cell[inside] // NX < 5)  # SDs reached the first piece
+    assert np.array_equal(got["gid"], inside)
+    assert np.array_equal(got["cell"], st.cell[inside])
+    assert np.array_equal(got["zeta"], zt[inside])
+    assert np.array_equal(got["xi"], st.xi[inside])
+    assert np.array_equal(got["v"], st.v[inside])
+
+
 def test_heights_round_trip_and_emigrants(env):
     """sdm_set_heights takes heights bit for bit; after a sedimentation step
     sdm_get_heights names, for an SD that left a piece through its bottom,

@@ -74,6 +74,12 @@ def test_noalloc_rejects_bad_sizes(env):
         sdm.sdm_cell_step_noalloc(cfg, 0, torch.ones(7, dtype=torch.int64, device=dev),
                                   torch.ones(7, dtype=torch.float64, device=dev), stream)
     assert e.value.status == sdm.SDM_EINVAL and "even" in str(e.value)
+    # a context's piece-of-grid offset has no meaning here (random streams of cell 0)
+    with pytest.raises(sdm.SdmError) as e:
+        sdm.sdm_cell_step_noalloc(sdm.make_config("golovin", n_cells=1, cell_base=8), 0,
+                                  torch.ones(64, dtype=torch.int64, device=dev),
+                                  torch.ones(64, dtype=torch.float64, device=dev), stream)
+    assert e.value.status == sdm.SDM_EINVAL
     # a volume array shorter than xi is refused on the host, before any launch
     with pytest.raises(ValueError):
         sdm.sdm_cell_step_noalloc(cfg, 0, torch.ones(64, dtype=torch.int64, device=dev),
