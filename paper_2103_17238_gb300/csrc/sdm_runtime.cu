@@ -146,6 +146,14 @@ struct Plan {
     WorkItem *d_items[kNumClass] = {};
     int n_items[kNumClass] = {};
     int variant[kNumClass] = {};
+    // A context's own plan whose cells all take the shared-memory classes
+    // keeps room for every cell in every class (class k at d_items_all + k
+    // n_cells), so that the device can rebuild it for a new layout
+    // (plan_refresh_kernel): refresh[0 .. kNumClass) are then the classes'
+    // counts, refresh[kNumClass] = 1 when a cell left those classes.
+    bool refreshable = false;
+    WorkItem *d_items_all = nullptr;
+    uint32_t *d_refresh = nullptr;
     WorkItem *d_mid[3] = {};     // cells of the cluster path, by cluster size K = 1, 2, 4, largest first
     int n_mid[3] = {};
     int mid_clusters[3] = {};    // clusters of each launch: the SMs dealt in proportion to the classes' SDs
@@ -214,6 +222,11 @@ struct sdm_ctx {
     cudaEvent_t in_ev[kInChunks + 1] = {};
     int64_t device_bytes = 0;
     sdm_batch *self_batch = nullptr;
+    // pinned host copy of the own batch's launch plan: uploaded from here,
+    // written again only after the event shows the last upload done
+    void *h_plan = nullptr;
+    size_t h_plan_bytes = 0;
+    cudaEvent_t plan_ev = nullptr;
 };
 
 namespace {
@@ -233,6 +246,7 @@ struct sdm_batch {
     int64_t *d_delta = nullptr;       // per-run step deltas for counter syncs
     std::vector<int64_t> h_delta;
     std::vector<int64_t> versions;    // the contexts' layout versions the plan was built for
+    sdm_ctx *own = nullptr;           // the context this batch belongs to (sdm_coalescence_step), if any
     std::string error;
     bool broken = false;
 };
@@ -569,43 +583,135 @@ int class_of(int n, const sdm_tuning &t)
     return c;
 }
 
+constexpr int kRefreshNT = 256;
+
+// The work items of a run whose cells all take the shared-memory classes,
+// from its cell offsets, as build_plan makes them (class_of): class k's at
+// items + k cap, their number added to counts[k]; counts[kNumClass] = 1 when
+// a cell is above smem_max_sd.  Block-level counts first, then one global
+// atomic per class and block (the order of a class's items is free: cells
+// are independent).
+__global__ void __launch_bounds__(kRefreshNT) plan_refresh_kernel(const int32_t *__restrict__ cell_off,
+                                                                  int32_t n_cells, int32_t cell_base,
+                                                                  int32_t smem_max_sd, WorkItem *__restrict__ items,
+                                                                  int32_t cap, uint32_t *__restrict__ counts)
+{
+    __shared__ uint32_t s_cnt[kNumClass], s_base[kNumClass];
+    if (threadIdx.x < kNumClass)
+        s_cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const int c = blockIdx.x * kRefreshNT + threadIdx.x;
+    int k = -1, o = 0, n = 0;
+    uint32_t slot = 0;
+    if (c < n_cells) {
+        o = cell_off[c];
+        n = cell_off[c + 1] - o;
+        if (n >= 2) {
+            k = n <= 64 ? 0 : 32 - __clz(n - 1) - 6;
+            if (k >= kNumClass || (64 << k) > smem_max_sd) {
+                counts[kNumClass] = 1u;
+                k = -1;
+            } else {
+                slot = atomicAdd(&s_cnt[k], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumClass)
+        s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+    if (k >= 0)
+        items[(int64_t)k * cap + s_base[k] + slot] = WorkItem{0, cell_base + c, o, n};
+}
+
+// Starts the device rebuild of a refreshable plan from the run's offsets.
+cudaError_t plan_refresh(Plan &pl, const int32_t *d_cell_off, int32_t n_cells, int32_t cell_base, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(pl.d_refresh, 0, sizeof(uint32_t) * (kNumClass + 1), st);
+    if (e != cudaSuccess || n_cells == 0)
+        return e;
+    plan_refresh_kernel<<<(n_cells + kRefreshNT - 1) / kRefreshNT, kRefreshNT, 0, st>>>(
+        d_cell_off, n_cells, cell_base, pl.tuning.smem_max_sd, pl.d_items_all, n_cells, pl.d_refresh);
+    return cudaGetLastError();
+}
+
 // Work lists of every run in the batch, split by cell size.
 sdm_status build_plan(sdm_batch *b)
 {
     Plan &pl = b->plan;
     DevMem &mem = b->mem;
     const int n_inst = (int)b->ctxs.size();
-    std::vector<WorkItem> items[kNumClass];
-    std::vector<WorkItem> mid[3];
-    std::vector<BigCell> bigs;
-    std::vector<BigChunk> chunks;
-    std::vector<BigBucket> buckets;
-    std::vector<BigPairs> pairs;
-    std::vector<InstDev *> insts(n_inst);
+    // the tables are gathered in host vectors kept by the thread, so that a
+    // plan rebuilt after every sedimentation step reuses their memory
+    struct Scratch {
+        std::vector<WorkItem> items[kNumClass];
+        std::vector<WorkItem> mid[3];
+        std::vector<BigCell> bigs;
+        std::vector<BigChunk> chunks;
+        std::vector<BigBucket> buckets;
+        std::vector<BigPairs> pairs;
+        std::vector<InstDev *> insts;
+        std::vector<int8_t> cls; // per cell of a run: its class, -1 above them, -2 fewer than 2 SDs
+    };
+    static thread_local Scratch scr;
+    std::vector<WorkItem>(&items)[kNumClass] = scr.items;
+    std::vector<WorkItem>(&mid)[3] = scr.mid;
+    std::vector<BigCell> &bigs = scr.bigs;
+    std::vector<BigChunk> &chunks = scr.chunks;
+    std::vector<BigBucket> &buckets = scr.buckets;
+    std::vector<BigPairs> &pairs = scr.pairs;
+    std::vector<InstDev *> &insts = scr.insts;
+    for (auto &v : items)
+        v.clear();
+    for (auto &v : mid)
+        v.clear();
+    bigs.clear();
+    chunks.clear();
+    buckets.clear();
+    pairs.clear();
+    insts.assign(n_inst, nullptr);
     int64_t hist_total = 0, sd_total = 0, bkt_total = 0;
     const sdm_tuning tun = current_tuning();
     pl.tuning = tun;
-    {
-        int64_t cells = 0;
-        for (int i = 0; i < n_inst; ++i)
-            cells += b->ctxs[i]->cfg.n_cells;
-        for (int k = 0; k < kNumClass; ++k)
-            items[k].reserve((size_t)cells);
-    }
     for (int k = 0; k < kNumClass; ++k)
         pl.variant[k] = variant_for(kClassCap[k], tun);
     for (int i = 0; i < n_inst; ++i) {
         sdm_ctx *c = b->ctxs[i];
         insts[i] = c->d_inst;
-        for (int cell = 0; cell < c->cfg.n_cells; ++cell) {
-            const int n = c->h_cell_off[cell + 1] - c->h_cell_off[cell];
-            if (n < 2)
+        const int32_t *off = c->h_cell_off.data();
+        const int32_t nc = c->cfg.n_cells, cb = c->cfg.cell_base;
+        // the shared-memory classes in two tight passes (a class per cell and
+        // the classes' sizes, then the items into their places); the other
+        // cells after
+        std::vector<int8_t> &cls = scr.cls;
+        cls.resize((size_t)nc);
+        size_t cnt[kNumClass] = {};
+        bool above = false;
+        for (int32_t cell = 0; cell < nc; ++cell) {
+            const int n = off[cell + 1] - off[cell];
+            const int8_t k = n < 2 ? (int8_t)-2 : (int8_t)class_of(n, tun);
+            cls[cell] = k;
+            if (k >= 0)
+                ++cnt[k];
+            above |= k == -1;
+        }
+        WorkItem *dst[kNumClass];
+        for (int k = 0; k < kNumClass; ++k) {
+            const size_t at = items[k].size();
+            items[k].resize(at + cnt[k]);
+            dst[k] = items[k].data() + at;
+        }
+        for (int32_t cell = 0; cell < nc; ++cell) {
+            const int k = cls[cell];
+            if (k >= 0)
+                *dst[k]++ = WorkItem{i, cb + cell, off[cell], off[cell + 1] - off[cell]};
+        }
+        if (!above)
+            continue;
+        for (int cell = 0; cell < nc; ++cell) {
+            if (cls[cell] != -1)
                 continue;
-            const int cls = class_of(n, tun);
-            if (cls >= 0) {
-                items[cls].push_back(WorkItem{i, c->cfg.cell_base + cell, c->h_cell_off[cell], n});
-                continue;
-            }
+            const int n = off[cell + 1] - off[cell];
             if (n <= tun.mid_max_sd) { // the cluster path, K = 1, 2 or 4 CTAs (sorted below)
                 const int km = n <= kMidSdPerCta ? 0 : (n <= 2 * kMidSdPerCta ? 1 : 2);
                 mid[km].push_back(WorkItem{i, c->cfg.cell_base + cell, c->h_cell_off[cell], n});
@@ -660,8 +766,36 @@ sdm_status build_plan(sdm_batch *b)
     sz += a16(sizeof(BigBucket) * buckets.size());
     const size_t off_pairs = sz;
     sz += a16(sizeof(BigPairs) * pairs.size());
-    pl.host_pack.assign(sz, 0);
-    unsigned char *h = pl.host_pack.data();
+    // the own batch of a context uploads from the context's pinned copy (its
+    // last upload done first); other batches from a host vector of the plan
+    unsigned char *h = nullptr;
+    sdm_ctx *own = b->own;
+    if (own) {
+        if (own->plan_ev)
+            cudaEventSynchronize(own->plan_ev);
+        if (own->h_plan_bytes < sz) {
+            if (own->h_plan)
+                cudaFreeHost(own->h_plan);
+            own->h_plan = nullptr;
+            own->h_plan_bytes = 0;
+            const size_t want = sz + sz / 4 + 4096;
+            if (cudaMallocHost(&own->h_plan, want) == cudaSuccess)
+                own->h_plan_bytes = want;
+            else
+                cudaGetLastError();
+        }
+        if (own->h_plan && !own->plan_ev &&
+            cudaEventCreateWithFlags(&own->plan_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            own->plan_ev = nullptr;
+        }
+        if (own->h_plan && own->plan_ev)
+            h = static_cast<unsigned char *>(own->h_plan);
+    }
+    if (!h) {
+        pl.host_pack.assign(sz, 0);
+        h = pl.host_pack.data();
+    }
     std::memcpy(h, insts.data(), sizeof(InstDev *) * n_inst);
     for (int k = 0; k < kNumClass; ++k)
         if (!items[k].empty())
@@ -682,6 +816,21 @@ sdm_status build_plan(sdm_batch *b)
     for (int k = 0; k < kNumClass; ++k) {
         pl.n_items[k] = (int)items[k].size();
         pl.d_items[k] = pl.n_items[k] ? reinterpret_cast<WorkItem *>(d + off_items[k]) : nullptr;
+    }
+    // a context's own plan of shared-memory classes only: items with room
+    // for every cell in every class, built on the device like later refreshes
+    if (own && n_inst == 1 && bigs.empty() && mid[0].empty() && mid[1].empty() && mid[2].empty()) {
+        const int32_t nc = own->cfg.n_cells;
+        pl.d_items_all = plan_alloc<WorkItem>(pl, mem, (size_t)kNumClass * std::max(nc, 1));
+        pl.d_refresh = plan_alloc<uint32_t>(pl, mem, kNumClass + 1);
+        if (!pl.d_items_all || !pl.d_refresh)
+            return fail(&b->error, SDM_ENOMEM, "batch plan: device allocation failed");
+        pl.refreshable = true;
+        for (int k = 0; k < kNumClass; ++k)
+            pl.d_items[k] = pl.d_items_all + (size_t)k * nc;
+        const cudaError_t e = plan_refresh(pl, own->d_cell_off, nc, own->cfg.cell_base, b->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(b, e, "batch plan: work items");
     }
     for (int k = 0; k < 3; ++k) {
         pl.n_mid[k] = (int)mid[k].size();
@@ -740,10 +889,13 @@ sdm_status build_plan(sdm_batch *b)
             !pl.scratch.scale || !pl.scratch.scale_f)
             return fail(&b->error, SDM_ENOMEM, "batch plan: big-cell scratch allocation failed");
     }
-    // the host copy lives as long as the plan: no wait for the upload
-    const cudaError_t e = cudaMemcpyAsync(d, h, sz, cudaMemcpyHostToDevice, b->stream);
+    // the host copy lives as long as the plan (or, pinned, until the event
+    // below has passed): no wait for the upload
+    cudaError_t e = cudaMemcpyAsync(d, h, sz, cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess)
         return cuda_fail(b, e, "batch plan upload");
+    if (own && h == own->h_plan && (e = cudaEventRecord(own->plan_ev, b->stream)) != cudaSuccess)
+        return cuda_fail(b, e, "batch plan upload event");
     return SDM_OK;
 }
 
@@ -1362,6 +1514,7 @@ sdm_status sdm_coalescence_step(sdm_ctx *ctx, int32_t n_steps)
         if (!b)
             return fail(&ctx->error, SDM_ENOMEM, "host allocation failed");
         sdm_ctx *one[1] = {ctx};
+        b->own = ctx;
         st = batch_init(b, one, 1, ctx->stream, 0, 0);
         if (st != SDM_OK) {
             ctx->error = b->error;
@@ -1518,6 +1671,10 @@ sdm_status sdm_destroy(sdm_ctx *ctx)
     cond_release(ctx);
     ctx->mem.release_kept();
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (ctx->h_plan)
+        cudaFreeHost(ctx->h_plan);
+    if (ctx->plan_ev)
+        cudaEventDestroy(ctx->plan_ev);
     if (ctx->h_pin)
         cudaFreeHost(ctx->h_pin);
     if (ctx->h_spec)

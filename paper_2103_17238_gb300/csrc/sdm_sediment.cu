@@ -670,6 +670,15 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
                                                            b.id2, b.group2);
     CTX_CUDA(ctx, cudaGetLastError());
+    // the context's own launch plan, when refreshable, rebuilt on the device
+    // for the new layout (its class counts come back with the offsets)
+    sdm_batch *sb = ctx->self_batch;
+    const bool refresh = sb && sb->plan.refreshable && same_tuning(sb->plan.tuning, current_tuning());
+    uint32_t rc[kNumClass + 1] = {};
+    if (refresh) {
+        CTX_CUDA(ctx, plan_refresh(sb->plan, b.cell_off2, nc, ctx->cfg.cell_base, s));
+        CTX_CUDA(ctx, cudaMemcpyAsync(rc, sb->plan.d_refresh, sizeof rc, cudaMemcpyDeviceToHost, s));
+    }
     std::vector<int32_t> off(n_groups + 1);
     double precip = 0.0;
     CTX_CUDA(ctx, cudaMemcpyAsync(off.data(), b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
@@ -695,9 +704,13 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     ctx->dev_base = ctx->step;
     InstDev inst = make_inst(ctx);
     CTX_CUDA(ctx, cudaMemcpyAsync(ctx->d_inst, &inst, sizeof inst, cudaMemcpyHostToDevice, s));
-    if (ctx->self_batch && keep_plan)
+    const bool refreshed = refresh && !keep_plan && rc[kNumClass] == 0;
+    if (refreshed)
+        for (int k = 0; k < kNumClass; ++k)
+            ctx->self_batch->plan.n_items[k] = (int)rc[k];
+    if (ctx->self_batch && (keep_plan || refreshed))
         ctx->self_batch->versions[0] = ctx->layout_version;
-    if (ctx->self_batch && !keep_plan) {
+    if (ctx->self_batch && !keep_plan && !refreshed) {
         batch_release(ctx->self_batch);
         delete ctx->self_batch;
         ctx->self_batch = nullptr;
