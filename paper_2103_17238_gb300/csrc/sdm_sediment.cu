@@ -486,7 +486,12 @@ struct SedBuffers {
     uint32_t *hist = nullptr;   // 256 x tiles, then 256 digit totals
     uint32_t *flags = nullptr;  // flags, then the first bad id (8-byte aligned)
     int32_t *emig = nullptr;    // per SD id: its cell in another piece of the grid after the last step, or -1
+    void *h_read = nullptr;     // pinned: the new offsets, the precipitated total and the plan's class counts
 };
+
+// Bytes of the pinned read-back buffer for n_cells cells: n_cells + 2
+// offsets, the precipitated total (8-byte aligned) and 8 class-count words.
+size_t sed_read_bytes(int32_t n_cells) { return (((size_t)n_cells + 2) * 4 + 7) / 8 * 8 + 8 + 32; }
 
 void sed_release(sdm_ctx *ctx)
 {
@@ -497,6 +502,10 @@ void sed_release(sdm_ctx *ctx)
                         b.counts,   b.ustart,   b.precip,   b.hist,   b.flags,  b.emig};
         for (void *p : bufs)
             ctx->mem.put(p, 0);
+        if (b.h_read) {
+            cudaStreamSynchronize(ctx->stream); // no read-back in flight
+            cudaFreeHost(b.h_read);
+        }
         delete ctx->sed;
         ctx->sed = nullptr;
     }
@@ -540,9 +549,13 @@ sdm_status sed_alloc(sdm_ctx *ctx)
     b.hist = sed_get<uint32_t>(ctx, (size_t)kRadixBuckets * tiles + kRadixBuckets);
     b.flags = sed_get<uint32_t>(ctx, 4);
     b.emig = sed_get<int32_t>(ctx, cap);
+    if (cudaMallocHost(&b.h_read, sed_read_bytes(nc)) != cudaSuccess) {
+        cudaGetLastError();
+        b.h_read = nullptr;
+    }
     const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.group && b.group2 && b.cell_off2 &&
                     b.zeta_new && b.keys[0] && b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart &&
-                    b.precip && b.hist && b.flags && b.emig;
+                    b.precip && b.hist && b.flags && b.emig && b.h_read;
     if (!ok) {
         sed_release(ctx);
         return fail(&ctx->error, SDM_ENOMEM, "sedimentation buffers: device allocation failed");
@@ -674,16 +687,21 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     // for the new layout (its class counts come back with the offsets)
     sdm_batch *sb = ctx->self_batch;
     const bool refresh = sb && sb->plan.refreshable && same_tuning(sb->plan.tuning, current_tuning());
-    uint32_t rc[kNumClass + 1] = {};
+    // read back into the pinned buffer: offsets, precipitated total, counts
+    unsigned char *hr = static_cast<unsigned char *>(b.h_read);
+    const int32_t *off = reinterpret_cast<const int32_t *>(hr);
+    const size_t at_pr = (((size_t)nc + 2) * 4 + 7) / 8 * 8;
+    const uint32_t *rc = reinterpret_cast<const uint32_t *>(hr + at_pr + 8);
     if (refresh) {
         CTX_CUDA(ctx, plan_refresh(sb->plan, b.cell_off2, nc, ctx->cfg.cell_base, s));
-        CTX_CUDA(ctx, cudaMemcpyAsync(rc, sb->plan.d_refresh, sizeof rc, cudaMemcpyDeviceToHost, s));
+        CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr + 8, sb->plan.d_refresh, sizeof(uint32_t) * (kNumClass + 1),
+                                      cudaMemcpyDeviceToHost, s));
     }
-    std::vector<int32_t> off(n_groups + 1);
-    double precip = 0.0;
-    CTX_CUDA(ctx, cudaMemcpyAsync(off.data(), b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(&precip, b.precip + kSedMaxBlocks, sizeof precip, cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(hr, b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
+    CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr, b.precip + kSedMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
+    double precip = 0.0;
+    std::memcpy(&precip, hr + at_pr, sizeof precip);
     // the new layout becomes the state; the old one the next scratch
     std::swap(ctx->d_xi, b.xi2);
     std::swap(ctx->d_v, b.v2);
@@ -691,13 +709,13 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     std::swap(ctx->d_id_of_slot, b.id2);
     std::swap(ctx->d_cell_off, b.cell_off2);
     std::swap(b.group, b.group2);
-    std::vector<int32_t> cell_off(off.begin(), off.begin() + nc + 1);
     int32_t largest = 0;
     for (int32_t c = 0; c < nc; ++c)
-        largest = std::max(largest, cell_off[c + 1] - cell_off[c]);
-    const bool keep_plan = ctx->self_batch && ctx->h_cell_off == cell_off &&
+        largest = std::max(largest, off[c + 1] - off[c]);
+    const bool keep_plan = ctx->self_batch && ctx->h_cell_off.size() == (size_t)nc + 1 &&
+                           std::equal(ctx->h_cell_off.begin(), ctx->h_cell_off.end(), off) &&
                            same_tuning(ctx->self_batch->plan.tuning, current_tuning());
-    ctx->h_cell_off = cell_off;
+    ctx->h_cell_off.assign(off, off + nc + 1);
     ctx->n_slots = off[n_groups];
     ctx->largest_cell = largest;
     ctx->layout_version += 1;
