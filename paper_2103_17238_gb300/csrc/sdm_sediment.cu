@@ -254,8 +254,17 @@ __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restri
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     unsigned long long carry = 0;
     for (int32_t g0 = 0; g0 < n_groups; g0 += TILE) {
-        for (int i = t; i < TILE; i += 1024)
-            s_c[i] = g0 + i < n_groups ? counts[g0 + i] : 0u;
+        {
+            uint32_t c[E]; // the tile's loads all in flight at once
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = t + e * 1024;
+                c[e] = g0 + i < n_groups ? counts[g0 + i] : 0u;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                s_c[t + e * 1024] = c[e];
+        }
         __syncthreads();
         unsigned long long v[E], sum = 0;
 #pragma unroll
@@ -285,28 +294,47 @@ __global__ void __launch_bounds__(1024) sed_scan_kernel(const uint32_t *__restri
             s_w[lane] = w; // inclusive totals of warps 0 .. lane
         }
         __syncthreads();
-        unsigned long long base = carry + (warp > 0 ? s_w[warp - 1] : 0ull) + x - sum;
+        // the two results through shared memory, so that the writes to
+        // global memory are coalesced (consecutive threads, consecutive groups)
+        const unsigned long long base0 = carry + (warp > 0 ? s_w[warp - 1] : 0ull) + x - sum;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            const int32_t g = g0 + t * E + e;
-            if (g < n_groups) {
-                ustart[g] = (int32_t)(uint32_t)base;
-                poff[g] = (int32_t)(uint32_t)(base >> 32);
+        for (int half = 0; half < 2; ++half) {
+            unsigned long long base = base0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                s_c[t * E + e] = (uint32_t)(half ? base >> 32 : base);
+                base += v[e];
             }
-            base += v[e];
+            __syncthreads();
+            int32_t *out = half ? poff : ustart;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int32_t g = g0 + t + e * 1024;
+                if (g < n_groups)
+                    out[g] = (int32_t)s_c[t + e * 1024];
+            }
+            __syncthreads();
         }
         carry += s_w[31];
-        __syncthreads();
     }
     if (t == 0) {
         ustart[n_groups] = (int32_t)(uint32_t)carry;
         poff[n_groups] = (int32_t)(uint32_t)(carry >> 32);
     }
     // the precipitated water: thread t sums parts t, t + 1024, ... in order,
-    // then a fixed tree over the threads
+    // then a fixed tree over the threads (the loads of four parts in flight
+    // at once, the sums in the same order)
     double pr = 0.0;
-    for (int i = t; i < n_parts; i += 1024)
-        pr = __dadd_rn(pr, precip[i]);
+    for (int i0 = t; i0 < n_parts; i0 += 4 * 1024) {
+        double q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            q[u] = i0 + u * 1024 < n_parts ? precip[i0 + u * 1024] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u * 1024 < n_parts)
+                pr = __dadd_rn(pr, q[u]);
+    }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1)
         pr = __dadd_rn(pr, __shfl_down_sync(0xFFFFFFFFu, pr, d));
@@ -332,11 +360,16 @@ __global__ void __launch_bounds__(kRadixNT) radix_hist_kernel(const uint32_t *__
     h[t] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    uint32_t k[kRadixRounds]; // every load of the thread in flight at once
+#pragma unroll
     for (int r = 0; r < kRadixRounds; ++r) {
         const int64_t i = base + (int64_t)r * kRadixNT + t;
-        if (i < n)
-            atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+        k[r] = i < n ? keys[i] : 0xFFFFFFFFu;
     }
+#pragma unroll
+    for (int r = 0; r < kRadixRounds; ++r)
+        if (base + (int64_t)r * kRadixNT + t < n)
+            atomicAdd(&h[(k[r] >> shift) & 255u], 1u);
     __syncthreads();
     hist[(int64_t)t * n_tiles + blockIdx.x] = h[t];
 }
@@ -397,11 +430,19 @@ __global__ void __launch_bounds__(kRadixNT) radix_scatter_kernel(const uint32_t 
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
     const unsigned lt = (1u << lane) - 1u;
+    uint32_t kk[kRadixRounds], vv[kRadixRounds]; // every load of the thread in flight at once
+#pragma unroll
+    for (int r = 0; r < kRadixRounds; ++r) {
+        const int64_t i = base + (int64_t)r * kRadixNT + t;
+        kk[r] = i < n ? keys_in[i] : 0u;
+        vv[r] = i < n ? vals_in[i] : 0u;
+    }
+#pragma unroll
     for (int r = 0; r < kRadixRounds; ++r) {
         const int64_t i = base + (int64_t)r * kRadixNT + t;
         const bool valid = i < n;
-        const uint32_t k = valid ? keys_in[i] : 0u;
-        const uint32_t v = valid ? vals_in[i] : 0u;
+        const uint32_t k = kk[r];
+        const uint32_t v = vv[r];
         const uint32_t d = valid ? ((k >> shift) & 255u) : (uint32_t)kRadixBuckets;
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
         const uint32_t rank = (uint32_t)__popc(peers & lt);

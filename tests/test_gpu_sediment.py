@@ -96,6 +96,52 @@ def test_sedimentation_and_coalescence_interleaved(env, dt, rounds):
     run.close()
 
 
+def test_launch_plan_follows_the_layout(env):
+    """A context's own launch plan is rebuilt on the device after each
+    sedimentation step while its cells stay in the shared-memory classes.
+    Here SDs of the second level land in the bottom one, so its cells grow
+    past 4096 SDs (the plan goes back to the host, the cells to the cluster
+    path), and the tuning changes between steps (also back to the host);
+    every step against the oracle."""
+    O, sdm, torch = env
+    rng = np.random.default_rng(31)
+    nx, nz, dz, dt = 2, 4, 10.0, 40.0
+    sizes = [3800, 3800, 2000, 2000, 500, 500, 500, 500]
+    cell = np.concatenate([np.full(n, c, np.int32) for c, n in enumerate(sizes)])
+    n = len(cell)
+    level = cell // nx
+    r = np.where(level == 1, rng.uniform(45e-6, 55e-6, n), rng.uniform(5e-6, 15e-6, n))
+    v = 4.0 / 3.0 * np.pi * r**3
+    xi = rng.integers(1, 10**6, n).astype(np.int64)
+    z = level.astype(np.float64) * dz + rng.uniform(0.0, dz, n)
+    perm = rng.permutation(n)
+    xi, v, cell, z = xi[perm], v[perm], cell[perm], z[perm]
+    cfg = sdm.make_config("geometric", "fp64", dt=dt, dv=1e6, n_cells=nx * nz, seed=3)
+    P = O.params("geometric", dt=dt, dv=1e6, seed=3)
+    st = O.State(xi.copy(), v.copy(), cell.copy(), None, nx * nz)
+    zeta = O.zeta_of(z, cell, nx, dz)
+    sdm.sdm_set_tuning(None)
+    try:
+        run = sdm.Run(cfg, n).set_attributes(xi, v, cell).set_positions(z, nx, dz)
+        run.step(1)  # the plan: shared-memory classes only
+        O.step(P, st, 0)
+        for t in range(1, 5):
+            if t == 3:
+                sdm.sdm_set_tuning({"smem_max_sd": 1024, "warp_cell_max": 256, "warps_per_block": 2})
+            run.sediment()
+            O.sediment(P, st, nx, dz, zeta)
+            _compare(O, run, st, zeta, nx, dz, f"after sedimentation {t}")
+            run.step(1)
+            O.step(P, st, t)
+            _compare(O, run, st, zeta, nx, dz, f"after coalescence {t}")
+            if t == 1:
+                counts = np.bincount(st.cell[st.cell >= 0], minlength=nx * nz)
+                assert counts[:nx].max() > 4096, counts  # a bottom cell left the shared-memory classes
+        run.close()
+    finally:
+        sdm.sdm_set_tuning(None)
+
+
 def test_full_grid_sedimentation(env):
     """The 128 x 128 x 256 grid as a 128-column, 128-level domain of 10 m
     levels: two rounds of sedimentation and coalescence, every SD compared."""
