@@ -528,6 +528,8 @@ struct SedBuffers {
     uint32_t *flags = nullptr;  // flags, then the first bad id (8-byte aligned)
     int32_t *emig = nullptr;    // per SD id: its cell in another piece of the grid after the last step, or -1
     void *h_read = nullptr;     // pinned: the new offsets, the precipitated total and the plan's class counts
+    cudaStream_t side = nullptr; // the offset scan (and the plan's refresh) beside the radix sort
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Bytes of the pinned read-back buffer for n_cells cells: n_cells + 2
@@ -543,10 +545,19 @@ void sed_release(sdm_ctx *ctx)
                         b.counts,   b.ustart,   b.precip,   b.hist,   b.flags,  b.emig};
         for (void *p : bufs)
             ctx->mem.put(p, 0);
-        if (b.h_read) {
-            cudaStreamSynchronize(ctx->stream); // no read-back in flight
-            cudaFreeHost(b.h_read);
+        if (b.h_read || b.side) {
+            cudaStreamSynchronize(ctx->stream); // no read-back in flight, the side stream joined
+            if (b.side)
+                cudaStreamSynchronize(b.side);
         }
+        if (b.h_read)
+            cudaFreeHost(b.h_read);
+        if (b.side)
+            cudaStreamDestroy(b.side);
+        if (b.fork)
+            cudaEventDestroy(b.fork);
+        if (b.join)
+            cudaEventDestroy(b.join);
         delete ctx->sed;
         ctx->sed = nullptr;
     }
@@ -593,6 +604,13 @@ sdm_status sed_alloc(sdm_ctx *ctx)
     if (cudaMallocHost(&b.h_read, sed_read_bytes(nc)) != cudaSuccess) {
         cudaGetLastError();
         b.h_read = nullptr;
+    }
+    if (cudaStreamCreateWithFlags(&b.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        sed_release(ctx);
+        return fail(&ctx->error, SDM_ENOMEM, "sedimentation stream and events: creation failed");
     }
     const bool ok = ctx->d_zeta && b.xi2 && b.v2 && b.zeta2 && b.id2 && b.group && b.group2 && b.cell_off2 &&
                     b.zeta_new && b.keys[0] && b.keys[1] && b.vals[0] && b.vals[1] && b.counts && b.ustart &&
@@ -703,8 +721,28 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     sed_move_kernel<<<move_blocks, kSedNT, 0, s>>>(ctx->d_inst, nc, ctx->n_slots, ctx->nx, ctx->dz, (float)ctx->cfg.dt,
                                                    ctx->d_zeta, b.group, ctx->d_id_of_slot, b.keys[0], b.vals[0],
                                                    b.zeta_new, b.counts, b.precip, ctx->cfg.cell_base, b.emig);
-    sed_scan_kernel<<<1, 1024, 0, s>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, move_blocks,
-                                       b.precip + kSedMaxBlocks);
+    // the offset scan, the refresh of the context's own launch plan (when
+    // refreshable: rebuilt on the device for the new layout) and the read-back
+    // into the pinned buffer (offsets, precipitated total, class counts) on
+    // the side stream, beside the radix sort, which needs none of them
+    sdm_batch *sb = ctx->self_batch;
+    const bool refresh = sb && sb->plan.refreshable && same_tuning(sb->plan.tuning, current_tuning());
+    unsigned char *hr = static_cast<unsigned char *>(b.h_read);
+    const int32_t *off = reinterpret_cast<const int32_t *>(hr);
+    const size_t at_pr = (((size_t)nc + 2) * 4 + 7) / 8 * 8;
+    const uint32_t *rc = reinterpret_cast<const uint32_t *>(hr + at_pr + 8);
+    CTX_CUDA(ctx, cudaEventRecord(b.fork, s));
+    CTX_CUDA(ctx, cudaStreamWaitEvent(b.side, b.fork, 0));
+    sed_scan_kernel<<<1, 1024, 0, b.side>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, move_blocks,
+                                            b.precip + kSedMaxBlocks);
+    if (refresh) {
+        CTX_CUDA(ctx, plan_refresh(sb->plan, b.cell_off2, nc, ctx->cfg.cell_base, b.side));
+        CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr + 8, sb->plan.d_refresh, sizeof(uint32_t) * (kNumClass + 1),
+                                      cudaMemcpyDeviceToHost, b.side));
+    }
+    CTX_CUDA(ctx, cudaMemcpyAsync(hr, b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, b.side));
+    CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr, b.precip + kSedMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, b.side));
+    CTX_CUDA(ctx, cudaEventRecord(b.join, b.side));
     // stable sort of the new groups, SD-id order in
     const int bits = 32 - __builtin_clz((unsigned)nc | 1u);
     const int passes = (bits + 7) / 8;
@@ -719,27 +757,12 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
                                                          tiles, b.keys[cur ^ 1], b.vals[cur ^ 1]);
         cur ^= 1;
     }
+    CTX_CUDA(ctx, cudaStreamWaitEvent(s, b.join, 0));
     sed_gather_kernel<<<1216, 256, 0, s>>>(n, b.keys[cur], b.vals[cur], b.ustart, b.cell_off2, ctx->d_xi, ctx->d_v,
                                            b.zeta_new, ctx->d_id_of_slot, b.xi2, b.v2, b.zeta2, b.id2, b.group2);
     sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
                                                            b.id2, b.group2);
     CTX_CUDA(ctx, cudaGetLastError());
-    // the context's own launch plan, when refreshable, rebuilt on the device
-    // for the new layout (its class counts come back with the offsets)
-    sdm_batch *sb = ctx->self_batch;
-    const bool refresh = sb && sb->plan.refreshable && same_tuning(sb->plan.tuning, current_tuning());
-    // read back into the pinned buffer: offsets, precipitated total, counts
-    unsigned char *hr = static_cast<unsigned char *>(b.h_read);
-    const int32_t *off = reinterpret_cast<const int32_t *>(hr);
-    const size_t at_pr = (((size_t)nc + 2) * 4 + 7) / 8 * 8;
-    const uint32_t *rc = reinterpret_cast<const uint32_t *>(hr + at_pr + 8);
-    if (refresh) {
-        CTX_CUDA(ctx, plan_refresh(sb->plan, b.cell_off2, nc, ctx->cfg.cell_base, s));
-        CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr + 8, sb->plan.d_refresh, sizeof(uint32_t) * (kNumClass + 1),
-                                      cudaMemcpyDeviceToHost, s));
-    }
-    CTX_CUDA(ctx, cudaMemcpyAsync(hr, b.cell_off2, sizeof(int32_t) * (n_groups + 1), cudaMemcpyDeviceToHost, s));
-    CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr, b.precip + kSedMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, s));
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
     double precip = 0.0;
     std::memcpy(&precip, hr + at_pr, sizeof precip);
