@@ -21,6 +21,8 @@
 //                        row, a scan of the digit totals, a ranked scatter;
 //   sed_gather_kernel    the new layout, gathered from the old one;
 //   sed_pad_kernel       its padding slots.
+// The scan, the padding, the refresh of the context's own launch plan and
+// the read-back run on a side stream beside the radix sort.
 // The two layouts swap; the host reads the new offsets for the launch plan.
 //
 // Compiled as part of the library's single translation unit (included at the
@@ -735,6 +737,9 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     CTX_CUDA(ctx, cudaStreamWaitEvent(b.side, b.fork, 0));
     sed_scan_kernel<<<1, 1024, 0, b.side>>>(b.counts, n_groups, b.ustart, b.cell_off2, b.precip, move_blocks,
                                             b.precip + kSedMaxBlocks);
+    // the new layout's padding slots (the gather writes only the others)
+    sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, b.side>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
+                                                                b.id2, b.group2);
     if (refresh) {
         CTX_CUDA(ctx, plan_refresh(sb->plan, b.cell_off2, nc, ctx->cfg.cell_base, b.side));
         CTX_CUDA(ctx, cudaMemcpyAsync(hr + at_pr + 8, sb->plan.d_refresh, sizeof(uint32_t) * (kNumClass + 1),
@@ -760,8 +765,6 @@ extern "C" sdm_status sdm_sedimentation_step(sdm_ctx *ctx, double *precipitated)
     CTX_CUDA(ctx, cudaStreamWaitEvent(s, b.join, 0));
     sed_gather_kernel<<<1216, 256, 0, s>>>(n, b.keys[cur], b.vals[cur], b.ustart, b.cell_off2, ctx->d_xi, ctx->d_v,
                                            b.zeta_new, ctx->d_id_of_slot, b.xi2, b.v2, b.zeta2, b.id2, b.group2);
-    sed_pad_kernel<<<(n_groups + 255) / 256, 256, 0, s>>>(n_groups, b.ustart, b.cell_off2, b.xi2, b.v2, b.zeta2,
-                                                           b.id2, b.group2);
     CTX_CUDA(ctx, cudaGetLastError());
     CTX_CUDA(ctx, cudaStreamSynchronize(s));
     double precip = 0.0;
