@@ -154,6 +154,12 @@ struct Plan {
     bool refreshable = false;
     WorkItem *d_items_all = nullptr;
     uint32_t *d_refresh = nullptr;
+    // with several groups of work (size classes, the large-cell path), each
+    // size class launches on a stream of its own beside the others
+    cudaStream_t cls_side[kNumClass] = {};
+    cudaEvent_t cls_fork = nullptr, cls_join[kNumClass] = {};
+    cudaStream_t big_hi = nullptr; // then the large-cell path's, at the device's greatest priority
+    cudaEvent_t big_join = nullptr;
     WorkItem *d_mid[3] = {};     // cells of the cluster path, by cluster size K = 1, 2, 4, largest first
     int n_mid[3] = {};
     int mid_clusters[3] = {};    // clusters of each launch: the SMs dealt in proportion to the classes' SDs
@@ -312,6 +318,18 @@ void plan_free(Plan &pl, DevMem &mem)
     }
     if (pl.mid_fork)
         cudaEventDestroy(pl.mid_fork);
+    for (int k = 0; k < kNumClass; ++k) {
+        if (pl.cls_side[k])
+            cudaStreamDestroy(pl.cls_side[k]);
+        if (pl.cls_join[k])
+            cudaEventDestroy(pl.cls_join[k]);
+    }
+    if (pl.cls_fork)
+        cudaEventDestroy(pl.cls_fork);
+    if (pl.big_hi)
+        cudaStreamDestroy(pl.big_hi);
+    if (pl.big_join)
+        cudaEventDestroy(pl.big_join);
     pl = Plan{};
 }
 
@@ -869,6 +887,44 @@ sdm_status build_plan(sdm_batch *b)
             if (e != cudaSuccess)
                 return cuda_fail(b, e, "batch plan: side streams");
         }
+        // the size classes side by side when there is more than one group of
+        // work: those whose cells do not fill the device's resident blocks on
+        // their own (a class that fills them gains nothing beside another),
+        // and not when the multi-pass path holds more than 2^22 SDs (it then
+        // fills the device by itself, and the classes beside it only slowed
+        // it: 1.64e10 against 1.67e10 pair-updates/s on the 1024-box ensemble,
+        // while mixes of a few dozen runs stepped a third faster)
+        bool small[kNumClass] = {};
+        int groups = classes > 0 ? 1 : 0;
+        for (int k = 0; k < kNumClass; ++k) {
+            if (!pl.n_items[k])
+                continue;
+            ++groups;
+            const Variant &x = g_variants[pl.variant[k]];
+            small[k] = (int64_t)pl.n_items[k] < (int64_t)G.variant[pl.variant[k]] * (x.warps > 0 ? x.warps : 1);
+        }
+        if (groups > 1 && sd_total <= ((int64_t)1 << 22)) {
+            cudaError_t e = cudaEventCreateWithFlags(&pl.cls_fork, cudaEventDisableTiming);
+            for (int k = 0; k < kNumClass && e == cudaSuccess; ++k) {
+                if (!small[k])
+                    continue;
+                e = cudaStreamCreateWithFlags(&pl.cls_side[k], cudaStreamNonBlocking);
+                if (e == cudaSuccess)
+                    e = cudaEventCreateWithFlags(&pl.cls_join[k], cudaEventDisableTiming);
+            }
+            // the large-cell path (the critical one when present) ahead of the
+            // forked classes in the block scheduler
+            if (e == cudaSuccess && classes > 0) {
+                int least = 0, greatest = 0;
+                e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+                if (e == cudaSuccess)
+                    e = cudaStreamCreateWithPriority(&pl.big_hi, cudaStreamNonBlocking, greatest);
+                if (e == cudaSuccess)
+                    e = cudaEventCreateWithFlags(&pl.big_join, cudaEventDisableTiming);
+            }
+            if (e != cudaSuccess)
+                return cuda_fail(b, e, "batch plan: size-class streams");
+        }
     }
     if (!bigs.empty()) {
         pl.n_big = (int)bigs.size();
@@ -948,12 +1004,54 @@ void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
 }
 
 // Enqueues one step (offset `off` from each run's device counter) of every cell.
+// The size classes' launches on their own streams (forked from st, joined
+// back by join()), when the plan has them; else, and for a class that a
+// refresh of the plan on the device filled after it was built, on st.
+struct ClassFork {
+    const Plan &pl;
+    cudaStream_t st;
+    bool on;
+    ClassFork(const Plan &p, cudaStream_t s) : pl(p), st(s), on(p.cls_fork != nullptr)
+    {
+        if (!on)
+            return;
+        cudaEventRecord(pl.cls_fork, st);
+        for (int k = 0; k < kNumClass; ++k)
+            if (side(k))
+                cudaStreamWaitEvent(pl.cls_side[k], pl.cls_fork, 0);
+    }
+    bool side(int k) const { return on && pl.n_items[k] && pl.cls_side[k]; }
+    cudaStream_t of(int k) const { return side(k) ? pl.cls_side[k] : st; }
+    // the stream of the large-cell path (forked at the same point)
+    cudaStream_t big() const
+    {
+        if (!on || !pl.big_hi)
+            return st;
+        cudaStreamWaitEvent(pl.big_hi, pl.cls_fork, 0);
+        return pl.big_hi;
+    }
+    void join() const
+    {
+        for (int k = 0; k < kNumClass; ++k)
+            if (side(k)) {
+                cudaEventRecord(pl.cls_join[k], pl.cls_side[k]);
+                cudaStreamWaitEvent(st, pl.cls_join[k], 0);
+            }
+        if (on && pl.big_hi) {
+            cudaEventRecord(pl.big_join, pl.big_hi);
+            cudaStreamWaitEvent(st, pl.big_join, 0);
+        }
+    }
+};
+
 void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
 {
+    const ClassFork f(pl, st);
     for (int k = 0; k < kNumClass; ++k)
         if (pl.n_items[k])
-            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, st);
-    enqueue_big(pl, off, st);
+            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, f.of(k));
+    enqueue_big(pl, off, f.big());
+    f.join();
 }
 
 // Enqueues n steps (offsets off .. off + n - 1) of every cell.  Cells are
@@ -970,6 +1068,7 @@ void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
     }
     for (int32_t i = 0; i < n; i += f) {
         const int32_t m = std::min(f, n - i);
+        const ClassFork cf(pl, st);
         for (int k = 0; k < kNumClass; ++k) {
             if (!pl.n_items[k])
                 continue;
@@ -977,14 +1076,16 @@ void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
             if (x.warps > 0) {
                 const FusedVariant &fv = g_fused[k];
                 const int grid = std::min((pl.n_items[k] + 1) / 2, dev_grids().fused[k]);
-                fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, m, st);
+                fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, m, cf.of(k));
             } else {
                 for (int32_t j = 0; j < m; ++j)
-                    launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i + j, st);
+                    launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i + j, cf.of(k));
             }
         }
+        const cudaStream_t bs = cf.big();
         for (int32_t j = 0; j < m; ++j)
-            enqueue_big(pl, off + i + j, st);
+            enqueue_big(pl, off + i + j, bs);
+        cf.join();
     }
 }
 
