@@ -1003,7 +1003,6 @@ void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
     join();
 }
 
-// Enqueues one step (offset `off` from each run's device counter) of every cell.
 // The size classes' launches on their own streams (forked from st, joined
 // back by join()), when the plan has them; else, and for a class that a
 // refresh of the plan on the device filled after it was built, on st.
@@ -1044,49 +1043,36 @@ struct ClassFork {
     }
 };
 
-void enqueue_step(const Plan &pl, int64_t off, cudaStream_t st)
-{
-    const ClassFork f(pl, st);
-    for (int k = 0; k < kNumClass; ++k)
-        if (pl.n_items[k])
-            launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off, f.of(k));
-    enqueue_big(pl, off, f.big());
-    f.join();
-}
-
 // Enqueues n steps (offsets off .. off + n - 1) of every cell.  Cells are
 // independent, so each one may take its n steps apart from the others: with
 // fusion on (tuning fuse_steps f >= 2) the warp-per-cell classes take up to f
 // steps per launch, the other cells one launch per step.
 void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
 {
+    // one fork and one join for all n steps: every class's launches follow
+    // each other on its stream, the large-cell path's on its own, and no
+    // class waits for another between steps (their cells are independent)
+    const ClassFork cf(pl, st);
+    const cudaStream_t bs = cf.big();
     const int32_t f = pl.tuning.fuse_steps;
-    if (f < 2 || n < 2) {
-        for (int32_t i = 0; i < n; ++i)
-            enqueue_step(pl, off + i, st);
-        return;
-    }
-    for (int32_t i = 0; i < n; i += f) {
-        const int32_t m = std::min(f, n - i);
-        const ClassFork cf(pl, st);
-        for (int k = 0; k < kNumClass; ++k) {
-            if (!pl.n_items[k])
-                continue;
-            const Variant &x = g_variants[pl.variant[k]];
-            if (x.warps > 0) {
-                const FusedVariant &fv = g_fused[k];
-                const int grid = std::min((pl.n_items[k] + 1) / 2, dev_grids().fused[k]);
-                fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, m, cf.of(k));
-            } else {
-                for (int32_t j = 0; j < m; ++j)
-                    launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i + j, cf.of(k));
-            }
+    const bool fuse = f >= 2 && n >= 2;
+    for (int k = 0; k < kNumClass; ++k) {
+        if (!pl.n_items[k])
+            continue;
+        const Variant &x = g_variants[pl.variant[k]];
+        if (fuse && x.warps > 0) {
+            const FusedVariant &fv = g_fused[k];
+            const int grid = std::min((pl.n_items[k] + 1) / 2, dev_grids().fused[k]);
+            for (int32_t i = 0; i < n; i += f)
+                fv.launch(grid, pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, std::min(f, n - i), cf.of(k));
+        } else {
+            for (int32_t i = 0; i < n; ++i)
+                launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, cf.of(k));
         }
-        const cudaStream_t bs = cf.big();
-        for (int32_t j = 0; j < m; ++j)
-            enqueue_big(pl, off + i + j, bs);
-        cf.join();
     }
+    for (int32_t i = 0; i < n; ++i)
+        enqueue_big(pl, off + i, bs);
+    cf.join();
 }
 
 // A captured graph: n steps from the device counters, then the counters advance by n.
