@@ -955,13 +955,15 @@ sdm_status build_plan(sdm_batch *b)
     return SDM_OK;
 }
 
-// One step (offset `off` from each run's device counter) of every cell above
-// the shared-memory threshold: the cluster path, then the multi-pass path.
-void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
+// n steps (offsets off .. off + n - 1 from each run's device counter) of
+// every cell above the shared-memory threshold: the cluster path and the
+// multi-pass path.  The cluster sizes run side by side and beside the
+// multi-pass path (one fork and one join by events for all n steps; a graph
+// captures the same), each cluster size on its share of the SMs, the
+// multi-pass kernels on the rest; a cluster size's steps follow each other
+// on its stream, and the multi-pass path's on st.
+void enqueue_big_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
 {
-    // the cluster sizes side by side, and beside the multi-pass path (fork
-    // and join by events; a graph captures the same): each cluster size on
-    // its share of the SMs, the multi-pass kernels on the rest
     const bool fork = pl.mid_fork != nullptr;
     if (fork) {
         cudaEventRecord(pl.mid_fork, st);
@@ -970,37 +972,32 @@ void enqueue_big(const Plan &pl, int64_t off, cudaStream_t st)
                 cudaStreamWaitEvent(pl.mid_side[k], pl.mid_fork, 0);
     }
     auto side = [&](int k) { return fork ? pl.mid_side[k] : st; };
-    if (pl.n_mid[2])
-        launch_mid<4>(pl.mid_clusters[2], pl.n_mid[2], pl.d_mid[2], pl.d_insts, off, side(2));
-    if (pl.n_mid[1])
-        launch_mid<2>(pl.mid_clusters[1], pl.n_mid[1], pl.d_mid[1], pl.d_insts, off, side(1));
-    if (pl.n_mid[0])
-        launch_mid<1>(pl.mid_clusters[0], pl.n_mid[0], pl.d_mid[0], pl.d_insts, off, side(0));
-    auto join = [&]() {
-        if (!fork)
-            return;
+    for (int32_t i = 0; i < n; ++i) {
+        if (pl.n_mid[2])
+            launch_mid<4>(pl.mid_clusters[2], pl.n_mid[2], pl.d_mid[2], pl.d_insts, off + i, side(2));
+        if (pl.n_mid[1])
+            launch_mid<2>(pl.mid_clusters[1], pl.n_mid[1], pl.d_mid[1], pl.d_insts, off + i, side(1));
+        if (pl.n_mid[0])
+            launch_mid<1>(pl.mid_clusters[0], pl.n_mid[0], pl.d_mid[0], pl.d_insts, off + i, side(0));
+    }
+    for (int32_t i = 0; pl.n_big && i < n; ++i) {
+        const int64_t o = off + i;
+        const size_t hs = big_hist_smem(pl.max_big_lb);
+        big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, o);
+        const int tiles = std::max(1, (1 << pl.max_big_lb) / kBigColNT);
+        big_colscan_kernel<<<pl.n_big * tiles, kBigColNT, 0, st>>>(pl.d_bigs, tiles, pl.scratch);
+        big_scan_kernel<<<pl.n_big, kBigNT, big_hist_smem(kBigMaxLB), st>>>(pl.d_bigs, pl.d_insts, pl.scratch);
+        big_scatter_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, o);
+        big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.d_insts, pl.scratch,
+                                                                   o);
+        big_pairs_kernel<<<pl.n_pair_blocks, kPairNT, 0, st>>>(pl.d_pairs, pl.d_bigs, pl.d_insts, pl.scratch, o);
+    }
+    if (fork)
         for (int k = 0; k < 3; ++k)
             if (pl.n_mid[k]) {
                 cudaEventRecord(pl.mid_join[k], pl.mid_side[k]);
                 cudaStreamWaitEvent(st, pl.mid_join[k], 0);
             }
-    };
-    if (!pl.n_big) {
-        join();
-        return;
-    }
-    {
-        const size_t hs = big_hist_smem(pl.max_big_lb);
-        big_hist_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
-        const int tiles = std::max(1, (1 << pl.max_big_lb) / kBigColNT);
-        big_colscan_kernel<<<pl.n_big * tiles, kBigColNT, 0, st>>>(pl.d_bigs, tiles, pl.scratch);
-        big_scan_kernel<<<pl.n_big, kBigNT, big_hist_smem(kBigMaxLB), st>>>(pl.d_bigs, pl.d_insts, pl.scratch);
-        big_scatter_kernel<<<pl.n_chunks, kBigNT, hs, st>>>(pl.d_chunks, pl.d_bigs, pl.d_insts, pl.scratch, off);
-        big_bucket_sort_kernel<<<pl.n_buckets, kBucketNT, 0, st>>>(pl.d_buckets, pl.d_bigs, pl.d_insts, pl.scratch,
-                                                                   off);
-        big_pairs_kernel<<<pl.n_pair_blocks, kPairNT, 0, st>>>(pl.d_pairs, pl.d_bigs, pl.d_insts, pl.scratch, off);
-    }
-    join();
 }
 
 // The size classes' launches on their own streams (forked from st, joined
@@ -1070,8 +1067,7 @@ void enqueue_steps(const Plan &pl, int64_t off, int32_t n, cudaStream_t st)
                 launch_variant(pl.variant[k], pl.n_items[k], pl.d_items[k], pl.d_insts, off + i, cf.of(k));
         }
     }
-    for (int32_t i = 0; i < n; ++i)
-        enqueue_big(pl, off + i, bs);
+    enqueue_big_steps(pl, off, n, bs);
     cf.join();
 }
 
