@@ -618,7 +618,11 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
     }
 
     for (int k = 0; gw + k * nw < n_items; ++k) {
-        if (lane == 0) {
+        // Every warp's second cell is asked for only once its first has
+        // landed: the first cells of all warps then share the HBM alone at
+        // the start of the launch instead of with the second ones.
+        const bool defer = STAGES > 1 && k == 0;
+        if (lane == 0 && !defer) {
             issue(k + STAGES - 1, nxt);
             fetch(k + STAGES);
         }
@@ -627,11 +631,15 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
         if (!__all_sync(FULL, arrived)) {
             if (lane == 0) {
                 atomicOr(&insts[s_meta[sg].w]->status, 1u);
-                for (int kk = k; kk < k + STAGES; ++kk)
+                for (int kk = k; kk < k + (defer ? STAGES - 1 : STAGES); ++kk) // the copies issued
                     if (gw + kk * nw < n_items)
                         mbar_wait_bounded(&s_bar[kk % STAGES], (uint32_t)(kk / STAGES) & 1u);
             }
             return;
+        }
+        if (lane == 0 && defer) {
+            issue(STAGES - 1, nxt);
+            fetch(STAGES);
         }
         const int4 meta = s_meta[sg];
         const int n = meta.y;
