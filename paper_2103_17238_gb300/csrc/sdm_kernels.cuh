@@ -671,9 +671,15 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
         for (int rep = 0; rep < n_rep; ++rep) { // warp-uniform
         const int64_t s = s0 + rep;
 
+        if constexpr (BPL % 4 == 0) {
 #pragma unroll
-        for (int i = 0; i < BPL; ++i)
-            s_hist[lane + 32 * i] = 0u;
+            for (int i = 0; i < BPL / 4; ++i)
+                reinterpret_cast<uint4 *>(s_hist)[lane + 32 * i] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+#pragma unroll
+            for (int i = 0; i < BPL; ++i)
+                s_hist[lane + 32 * i] = 0u;
+        }
         __syncwarp();
 
         // Sort words of live SDs and their bucket slots.  A word holds the
@@ -710,12 +716,30 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
         __syncwarp();
 
         // bucket starts by a warp scan; the total is n_c
+        // each lane's BPL buckets are contiguous: read and written as vectors
+        // (scalar accesses at this lane stride would conflict 8 ways at 256 SDs)
         uint32_t cnt[BPL], sum = 0;
+        if constexpr (BPL % 4 == 0) {
 #pragma unroll
-        for (int i = 0; i < BPL; ++i) {
-            cnt[i] = s_hist[lane * BPL + i];
-            sum += cnt[i];
+            for (int i = 0; i < BPL; i += 4) {
+                const uint4 t = reinterpret_cast<const uint4 *>(s_hist + lane * BPL + i)[0];
+                cnt[i] = t.x;
+                cnt[i + 1] = t.y;
+                cnt[i + 2] = t.z;
+                cnt[i + 3] = t.w;
+            }
+        } else if constexpr (BPL == 2) {
+            const uint2 t = reinterpret_cast<const uint2 *>(s_hist)[lane];
+            cnt[0] = t.x;
+            cnt[1] = t.y;
+        } else {
+#pragma unroll
+            for (int i = 0; i < BPL; ++i)
+                cnt[i] = s_hist[lane * BPL + i];
         }
+#pragma unroll
+        for (int i = 0; i < BPL; ++i)
+            sum += cnt[i];
         uint32_t incl = sum;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -727,8 +751,21 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
         uint32_t run = incl - sum;
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            s_hist[lane * BPL + i] = run;
-            run += cnt[i];
+            const uint32_t c = cnt[i];
+            cnt[i] = run; // the bucket's start
+            run += c;
+        }
+        if constexpr (BPL % 4 == 0) {
+#pragma unroll
+            for (int i = 0; i < BPL; i += 4)
+                reinterpret_cast<uint4 *>(s_hist + lane * BPL + i)[0] =
+                    make_uint4(cnt[i], cnt[i + 1], cnt[i + 2], cnt[i + 3]);
+        } else if constexpr (BPL == 2) {
+            reinterpret_cast<uint2 *>(s_hist)[lane] = make_uint2(cnt[0], cnt[1]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < BPL; ++i)
+                s_hist[lane * BPL + i] = cnt[i];
         }
         __syncwarp();
 
@@ -784,13 +821,14 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
                     v[E - 1] = next_first;
                 sort_net<E>(v);
             }
+            // two different words share their key bits iff 1 <= (a ^ b) <= RM
             bool prefix_tie = false;
 #pragma unroll
             for (int i = 0; i + 1 < E; ++i)
-                prefix_tie |= ((v[i] ^ v[i + 1]) <= RM) & (v[i] != v[i + 1]);
+                prefix_tie |= ((v[i] ^ v[i + 1]) - 1u) < RM;
             const uint32_t nf = __shfl_down_sync(FULL, v[0], 1);
             if (lane < 31)
-                prefix_tie |= ((v[E - 1] ^ nf) <= RM) & (v[E - 1] != nf);
+                prefix_tie |= ((v[E - 1] ^ nf) - 1u) < RM;
             if (fast && !__any_sync(FULL, prefix_tie)) {
                 uint32_t pk[E / 2];
 #pragma unroll
@@ -853,6 +891,9 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
 #pragma unroll
                 for (int r = 0; r < QG; ++r) {
                     const uint32_t q = q0 + lane + 32 * r;
+                    uint2 ab2 = make_uint2(0u, 0u); // pairs 2q and 2q + 1
+                    if (q < n_q)
+                        ab2 = reinterpret_cast<const uint2 *>(s_perm)[q];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t l = 2 * q + h;
@@ -861,7 +902,7 @@ __global__ void __launch_bounds__(32 * WARPS, (CAP <= 256) ? 20 / WARPS : 0) war
                         if (q < n_q && l < n_pairs) {
                             // the bound needs xi_j = max(xi_a, xi_b) only; which of the
                             // two is j is settled in the full pass
-                            const uint32_t ab = reinterpret_cast<const uint32_t *>(s_perm)[l];
+                            const uint32_t ab = h ? ab2.y : ab2.x;
                             const uint32_t a = ab & 0xFFFFu, b = ab >> 16;
                             const int64_t xa = xs[a], xb = xs[b];
                             abv[2 * r + h] = ab;
