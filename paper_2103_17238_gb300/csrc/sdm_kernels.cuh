@@ -1007,6 +1007,8 @@ struct BigPairs {
     int32_t big, q0; // pair-of-pairs indices q0 .. q0 + kPairNT - 1
 };
 
+constexpr int kLiveWords = kBigChunk / 32; // liveness bits of a chunk, in words
+
 struct BigScratch {
     uint32_t *hist;     // per (chunk, bucket) counts, then prefixes
     uint32_t *bstart;   // bucket starts per cell, last entry = n_c
@@ -1014,33 +1016,68 @@ struct BigScratch {
     uint32_t *perm;     // ranks in sorted order
     double *scale;      // per big cell
     float *scale_f;
+    uint32_t *live = nullptr; // kLiveWords per chunk of the launch: which SDs the histogram pass
+                              // found live, for the scatter pass (null: the scatter reads xi again)
 };
 
-// live SDs of one chunk: keys and their bucket; calls f(key, rank)
+// live SDs of one chunk: keys and their bucket; calls f(key, rank).  Every
+// thread of the block calls it.  Liveness comes from xi (live_in null; its
+// bits then go to live_out unless that is null too) or from the bits a
+// previous call of the same step wrote for the same chunk (live_in): word
+// 2 (32 i + warp) + h, bit `lane`, is SD 2q + h of the thread's i-th pair q.
 template <typename F>
 __device__ __forceinline__ void big_chunk_keys(const InstDev *P, const BigCell &bc, int chunk, int64_t s,
-                                               const int64_t *gxi, F &&f)
+                                               const int64_t *gxi, uint32_t *live_out, const uint32_t *live_in,
+                                               F &&f)
 {
     constexpr int QPT = kBigChunk / 2 / kBigNT; // SD pairs per thread
     static_assert(QPT * kBigNT * 2 == kBigChunk, "chunk = threads x pairs");
+    static_assert(2 * QPT * (kBigNT / 32) == kLiveWords, "a chunk's liveness words");
     const int lo2 = (chunk * kBigChunk) / 2;
     const int hi2 = min((chunk + 1) * kBigChunk, bc.n) / 2;
-    // every load of the thread first, so that they are in flight together
-    longlong2 x[QPT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool lx[QPT], ly[QPT];
+    if (live_in) {
+        uint2 m[QPT];
 #pragma unroll
-    for (int i = 0; i < QPT; ++i) {
-        const int q = lo2 + (int)threadIdx.x + i * kBigNT;
-        x[i] = q < hi2 ? reinterpret_cast<const longlong2 *>(gxi)[q] : make_longlong2(0, 0);
+        for (int i = 0; i < QPT; ++i)
+            m[i] = reinterpret_cast<const uint2 *>(live_in)[i * (kBigNT / 32) + warp];
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            lx[i] = (m[i].x >> lane) & 1u;
+            ly[i] = (m[i].y >> lane) & 1u;
+        }
+    } else {
+        // every load of the thread first, so that they are in flight together
+        longlong2 x[QPT];
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            const int q = lo2 + (int)threadIdx.x + i * kBigNT;
+            x[i] = q < hi2 ? reinterpret_cast<const longlong2 *>(gxi)[q] : make_longlong2(0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < QPT; ++i) {
+            lx[i] = x[i].x > 0;
+            ly[i] = x[i].y > 0;
+        }
+        if (live_out) {
+#pragma unroll
+            for (int i = 0; i < QPT; ++i) {
+                const unsigned bx = __ballot_sync(0xFFFFFFFFu, lx[i]), by = __ballot_sync(0xFFFFFFFFu, ly[i]);
+                if (lane == 0)
+                    reinterpret_cast<uint2 *>(live_out)[i * (kBigNT / 32) + warp] = make_uint2(bx, by);
+            }
+        }
     }
     const uint64_t seed = P->seed;
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
         const int q = lo2 + (int)threadIdx.x + i * kBigNT;
-        if ((x[i].x > 0) | (x[i].y > 0)) {
+        if (lx[i] | ly[i]) {
             const uint4 w = draw4(seed, (uint32_t)q, (uint32_t)bc.rcell, s, 0u);
-            if (x[i].x > 0)
+            if (lx[i])
                 f(((uint64_t)w.x << 32) | w.y, (uint32_t)(2 * q));
-            if (x[i].y > 0)
+            if (ly[i])
                 f(((uint64_t)w.z << 32) | w.w, (uint32_t)(2 * q + 1));
         }
     }
@@ -1063,7 +1100,9 @@ __global__ void __launch_bounds__(kBigNT) big_hist_kernel(const BigChunk *__rest
     const int64_t s = P->step + step_offset;
     const int64_t *gxi = P->xi + P->cell_off[bc.cell];
     const int sh = 64 - bc.lb;
-    big_chunk_keys(P, bc, ch.chunk, s, gxi, [&](uint64_t k, uint32_t) { atomicAdd(&s_hist[k >> sh], 1u); });
+    uint32_t *live = S.live ? S.live + (size_t)blockIdx.x * kLiveWords : nullptr;
+    big_chunk_keys(P, bc, ch.chunk, s, gxi, live, nullptr,
+                   [&](uint64_t k, uint32_t) { atomicAdd(&s_hist[k >> sh], 1u); });
     __syncthreads();
     uint32_t *h = S.hist + bc.hist_base + (int64_t)ch.chunk * NB;
     for (int i = threadIdx.x; i < NB; i += kBigNT)
@@ -1153,7 +1192,10 @@ __global__ void __launch_bounds__(kBigNT) big_scatter_kernel(const BigChunk *__r
     uint32_t *rout = S.rank + bc.sd_base;
     // only the rank is stored (4 bytes, not 12 with the key): the scattered
     // writes then stay in L2 instead of costing partial-sector rewrites
-    big_chunk_keys(P, bc, ch.chunk, s, gxi, [&](uint64_t k, uint32_t rank) {
+    // liveness as the histogram pass of this step found it (same chunk
+    // list and grid), so xi is not read again
+    const uint32_t *live = S.live ? S.live + (size_t)blockIdx.x * kLiveWords : nullptr;
+    big_chunk_keys(P, bc, ch.chunk, s, gxi, nullptr, live, [&](uint64_t k, uint32_t rank) {
         rout[atomicAdd(&s_cnt[(uint32_t)(k >> sh)], 1u)] = rank;
     });
 }

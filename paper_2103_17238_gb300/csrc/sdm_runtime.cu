@@ -941,8 +941,9 @@ sdm_status build_plan(sdm_batch *b)
         pl.scratch.perm = plan_alloc<uint32_t>(pl, mem, sd_total);
         pl.scratch.scale = plan_alloc<double>(pl, mem, bigs.size());
         pl.scratch.scale_f = plan_alloc<float>(pl, mem, bigs.size());
+        pl.scratch.live = plan_alloc<uint32_t>(pl, mem, chunks.size() * kLiveWords);
         if (!pl.scratch.hist || !pl.scratch.bstart || !pl.scratch.rank || !pl.scratch.perm ||
-            !pl.scratch.scale || !pl.scratch.scale_f)
+            !pl.scratch.scale || !pl.scratch.scale_f || !pl.scratch.live)
             return fail(&b->error, SDM_ENOMEM, "batch plan: big-cell scratch allocation failed");
     }
     // the host copy lives as long as the plan (or, pinned, until the event
@@ -1343,10 +1344,11 @@ int64_t sdm_footprint_bytes(int64_t capacity_sd, int32_t n_cells, int32_t larges
     // small per-call scratch kept between calls, by the context and by its own batch
     bytes += 2 * (int64_t)(DevMem::kKeepBlocks * DevMem::kKeepMax);
     if (largest_cell > current_tuning().smem_max_sd) {
-        // big-cell scratch, at most: rank and perm per SD; counts per chunk and bucket
+        // big-cell scratch, at most: rank and perm per SD; counts per chunk and bucket;
+        // liveness bits per chunk
         const int lb = big_lb(largest_cell);
         const int64_t chunks = (capacity_sd + kBigChunk - 1) / kBigChunk + n_cells;
-        bytes += capacity_sd * (4 + 4) + (chunks << lb) * 4 + ((int64_t)n_cells << lb) * 4;
+        bytes += capacity_sd * (4 + 4) + (chunks << lb) * 4 + ((int64_t)n_cells << lb) * 4 + chunks * kLiveWords * 4;
     }
     return bytes;
 }
