@@ -982,9 +982,9 @@ constexpr int kBigChunk = 8192;   // SDs per CTA in the histogram and scatter pa
 constexpr int kBigNT = 1024;
 constexpr int kBigMaxLB = 14;     // at most 16384 top-level buckets
 constexpr int kBucketCap = 1536;  // entries sorted in shared memory per bucket (1024 expected)
-constexpr int kBucketNT = 256;
+constexpr int kBucketNT = 128;
 constexpr int kSubLB = 9;         // second-level buckets inside a bucket
-constexpr int kPairNT = 256;
+constexpr int kPairNT = 128;
 
 struct BigCell {
     int32_t inst, cell;
